@@ -1,0 +1,334 @@
+"""Pins of the oracle's DSRG-MRPT2/PT3 energies (Sec. II.B).
+
+Each check is fixed by something other than the oracle itself: closed forms,
+brute-force perturbation theory in an explicit Fock space, exact operator
+matrices, and invariances the method must satisfy.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dsrg
+from oracle import fockspace as fsm
+
+from _fock_helpers import mr_fock_instance, product_dets_signs
+
+
+# ----------------------------------------------------------------------------
+# single-reference limits (no active orbitals)
+# ----------------------------------------------------------------------------
+
+def _sr_fock_pt3(inst):
+    """DSRG-PT3 of a single determinant with explicit matrices only.
+
+    For one determinant the one- and two-body non-diagonal parts of an
+    operator are its matrix elements between the determinant and its single
+    and double excitations, and three-body parts cannot reach the energy, so
+    Eqs. T2_1st..E(3) can be evaluated without any normal-order algebra.
+    Also returns MP2/MP3 by Rayleigh-Schroedinger theory with
+    H0 = sum_p eps_p {a+_p a_p}.
+    """
+    P = dsrg.SpinOrbitalProblem(inst)
+    n, s = P.nso, P.s
+    occ = list(np.where(P.hole)[0])
+    fs = fsm.FockSpace(n, len(occ), kmax=2)
+    g = P.gamma
+    lam = {2: np.zeros((0,) * 4), 3: np.zeros((0,) * 6)}
+    NO = lambda Z, k: fsm.quasiparticle_normal_ordered(fs, Z, k, occ)
+    phi = np.zeros(fs.dim)
+    b = 0
+    for i in occ:
+        b |= 1 << int(i)
+    phi[fs.sec[0].index[b]] = 1.0
+    H0 = NO(np.diag(P.eps), 1)
+    H1 = NO(P.V, 2) + NO(P.f1, 1)
+    hole = np.where(P.hole)[0]
+    part = np.where(P.part)[0]
+    exc = lambda ops: fsm._string_matrix(fs, ops) @ phi
+    singles = [(a, i, exc([("c", a), ("a", i)])) for a in part for i in hole]
+    doubles = [(a, b_, i, j, exc([("c", a), ("c", b_), ("a", j), ("a", i)]))
+               for a in part for b_ in part if a < b_ for i in hole for j in hole if i < j]
+    e = P.eps
+    R = lambda D: float(dsrg.regulariser(s, np.array(D)))
+
+    def amps(M):
+        T1 = np.zeros((n, n))
+        T2 = np.zeros((n,) * 4)
+        for a, i, v in singles:
+            T1[a, i] = (v @ M @ phi) * R(e[i] - e[a])
+        for a, b_, i, j, v in doubles:
+            x = (v @ M @ phi) * R(e[i] + e[j] - e[a] - e[b_])
+            T2[a, b_, i, j], T2[b_, a, i, j], T2[a, b_, j, i], T2[b_, a, j, i] = x, -x, -x, x
+        return T1, T2
+
+    c = lambda X, Y: X @ Y - Y @ X
+    T1, T2 = amps(H1)
+    Tm = NO(T1, 1) + NO(T2, 2)
+    Am = Tm - Tm.T
+    W = c(H0, Am)
+    Ht1 = 2 * H1 + W
+    E2 = phi @ c(Ht1, Tm) @ phi
+    O = 0.5 * c(Ht1, Am)
+    U1, U2 = amps(O)
+    Tb = NO(U1, 1) + NO(U2, 2)
+    Ab = Tb - Tb.T
+    Ht2 = c(H0, Ab) + O - c(W, Am) / 6.0
+    E3a = phi @ c(Ht1, Tb) @ phi
+    E3b = phi @ c(Ht2, Tm) @ phi
+    d0 = np.diag(H0)
+    shift = d0 - d0 @ (phi * phi)
+    Rm = np.where(np.abs(shift) < 1e-14, 0.0, 1.0 / np.where(np.abs(shift) < 1e-14, 1.0, shift))
+    psi1 = -Rm * (H1 @ phi)
+    return dict(e2=E2, e3a=E3a, e3b=E3b, mp2=phi @ H1 @ psi1,
+                mp3=psi1 @ H1 @ psi1 - (phi @ H1 @ phi) * (psi1 @ psi1))
+
+
+def _sr_instance(s, seed=12, nc=2, nv=3, naux=8):
+    inst = synth.make_instance(nc, 0, 0, nv, naux, s, seed=seed, eps_core=(-0.6, -0.1), eps_vir=(0.1, 0.6))
+    inst["B"] = inst["B"] * 3.0
+    return inst
+
+
+@pytest.mark.parametrize("s", [0.5, 3.0])
+def test_sr_pt3_equals_explicit_fock_space(s):
+    inst = _sr_instance(s)
+    r = dsrg.dsrg_pt3(inst)
+    f = _sr_fock_pt3(inst)
+    for k in ("e2", "e3a", "e3b"):
+        assert abs(r[k] - f[k]) < 1e-12 * max(1.0, abs(f[k])), k
+    assert abs(r["e3b"]) > 1e-3  # the Htilde^(2) term is exercised
+
+
+def test_sr_pt2_closed_form():
+    """a = 0: E(2)(s) = 1/4 sum |<ij||ab>|^2 (1 - exp(-2 s D^2)) / D."""
+    inst = _sr_instance(0.8, seed=3, nc=2, nv=4, naux=9)
+    r = dsrg.dsrg_pt3(inst, pt2_only=True, return_intermediates=True)
+    P = r["_problem"]
+    h, p = P.hole, P.part
+    V = P.V[np.ix_(p, p, h, h)]
+    D = P.D2[np.ix_(p, p, h, h)]
+    ref = 0.25 * np.sum(V ** 2 * (-np.expm1(-2 * P.s * D ** 2)) / D)
+    assert abs(r["e2"] - ref) < 1e-13 * abs(ref)
+
+
+def test_sr_infinite_s_is_mp2_mp3():
+    inst = _sr_instance(1.0e6)
+    r = dsrg.dsrg_pt3(inst)
+    f = _sr_fock_pt3(inst)
+    assert abs(r["e2"] - f["mp2"]) < 1e-12 * abs(f["mp2"])
+    assert abs(r["e3"] - f["mp3"]) < 1e-11 * abs(f["mp3"])
+
+
+# ----------------------------------------------------------------------------
+# multireference
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(1, 2, 2, 1, 4), (1, 3, 4, 1, 5), (0, 3, 2, 2, 5)])
+def test_mr_pt2_equals_fock_space(shape):
+    nc, na, nel, nv, naux = shape
+    inst, fs, psi, g, act, lam = mr_fock_instance(nc, na, nel, nv, naux, 0.5, seed=sum(shape))
+    r = dsrg.dsrg_pt3(inst, pt2_only=True, return_intermediates=True)
+    P, I = r["_problem"], r["_inter"]
+    NO = lambda Z, k: fsm.normal_ordered(fs, Z, k, g, act, lam)
+    H0 = NO(np.diag(P.eps), 1)
+    H1 = NO(P.V, 2)
+    Tm = NO(I["T1"], 1) + NO(I["T2"], 2)
+    Am = Tm - Tm.T
+    W = H0 @ Am - Am @ H0
+    Ht1 = 2 * H1 + W
+    E2 = psi @ (Ht1 @ Tm - Tm @ Ht1) @ psi
+    assert abs(E2 - r["e2"]) < 1e-12 * max(1, abs(E2))
+    # [H0, A1] has only the blocks the engine produced (Sec. II.B: W non-diagonal)
+    Wm = fsm.operator_matrix(fs, I["W"].c0, I["W"].z, g, act, lam)
+    assert np.abs(Wm - W).max() < 1e-12 * max(1, np.abs(W).max())
+    # <[H, A]> = 2 <[H, T]> (text after Eq. E(3))
+    assert abs(psi @ (Ht1 @ Am - Am @ Ht1) @ psi - 2 * E2) < 1e-11 * max(1, abs(E2))
+
+
+def test_w_has_only_nondiagonal_blocks():
+    inst, *_ = mr_fock_instance(1, 2, 2, 2, 5, 0.5, seed=8)
+    r = dsrg.dsrg_pt3(inst, pt2_only=True, return_intermediates=True)
+    P, W = r["_problem"], r["_inter"]["W"]
+    h, p, c, v = P.hole, P.part, P.core, P.vir
+    W1 = W.z[1]
+    # no core-core, virtual-virtual or core-virtual-in-wrong-direction one-body parts
+    assert np.abs(W1[np.ix_(c, c)]).max() < 1e-14
+    assert np.abs(W1[np.ix_(v, v)]).max() < 1e-14
+    W2 = W.z[2]
+    assert np.abs(W2[np.ix_(v, v, v, v)]).max() < 1e-14
+    assert np.abs(W2[np.ix_(c, c, c, c)]).max() < 1e-14
+    assert abs(W.c0) < 1e-13
+
+
+def _energies(inst):
+    r = dsrg.dsrg_pt3(inst)
+    return np.array([r["e2"], r["e3a"], r["e3b"]])
+
+
+def _small_mr(seed=5, s=0.5):
+    return synth.make_instance(1, 3, 2, 4, 10, s, seed=seed)
+
+
+def test_flow_parameter_zero_limit():
+    """T = O(s): E(2) = O(s) and E(3) = O(s^2) as s -> 0."""
+    base = _small_mr()
+    vals = []
+    for s in (1e-7, 1e-8):
+        inst = dict(base, s=s)
+        e = _energies(inst)
+        vals.append((e[0] / s, (e[1] + e[2]) / s ** 2))
+    (a2, a3), (b2, b3) = vals
+    assert abs(a2 - b2) < 2e-2 * abs(b2)
+    assert abs(a3 - b3) < 2e-2 * abs(b3)
+
+
+def test_homogeneity_in_integrals():
+    """With no off-diagonal Fock term, B -> c B scales E(2) by c^4, E(3) by c^6."""
+    base = _small_mr(seed=6)
+    e1 = _energies(base)
+    c = 1.7
+    e2 = _energies(dict(base, B=base["B"] * c))
+    assert np.allclose(e2[0], c ** 4 * e1[0], rtol=1e-12)
+    assert np.allclose(e2[1:], c ** 6 * e1[1:], rtol=1e-11)
+
+
+def test_auxiliary_rotation_invariance():
+    base = _small_mr(seed=7)
+    rng = np.random.default_rng(0)
+    Q = np.linalg.qr(rng.standard_normal((base["naux"], base["naux"])))[0]
+    rot = dict(base, B=np.einsum("PQ,Qpq->Ppq", Q, base["B"]))
+    assert np.allclose(_energies(rot), _energies(base), rtol=1e-12, atol=1e-14)
+
+
+def test_orbital_permutation_invariance():
+    base = _small_mr(seed=8)
+    nc, na, nv = base["nc"], base["na"], base["nv"]
+    n = nc + na + nv
+    perm = np.arange(n)
+    perm[nc + na:] = nc + na + np.random.default_rng(1).permutation(nv)
+    pm = dict(base, eps=base["eps"][perm], B=base["B"][:, perm][:, :, perm])
+    assert np.allclose(_energies(pm), _energies(base), rtol=1e-12, atol=1e-14)
+
+
+def test_spin_flip_invariance():
+    base = _small_mr(seed=9)
+    fl = dict(base)
+    fl["g1a"], fl["g1b"] = base["g1b"], base["g1a"]
+    fl["l2aa"], fl["l2bb"] = base["l2bb"], base["l2aa"]
+    fl["l2ab"] = np.transpose(base["l2ab"], (1, 0, 3, 2))
+    fl["l3aaa"], fl["l3bbb"] = base["l3bbb"], base["l3aaa"]
+    # lambda'[aU aV bW, aX aY bZ] = lambda[bU bV aW, bX bY aZ] = l3abb[W,U,V,Z,X,Y]
+    fl["l3aab"] = np.transpose(base["l3abb"], (1, 2, 0, 4, 5, 3))
+    fl["l3abb"] = np.transpose(base["l3aab"], (2, 0, 1, 5, 3, 4))
+    assert np.allclose(_energies(fl), _energies(base), rtol=1e-12, atol=1e-14)
+
+
+def test_size_consistency():
+    """Two non-interacting copies (Abstract, Sec. I): E(A+A) = 2 E(A)."""
+    nc, na, nel, nv, naux = 1, 2, 2, 2, 6
+    inst = synth.make_instance(nc, na, nel, nv, naux, 0.5, seed=31)
+    ref1 = synth.reference_from_ci(na, nel, rng=np.random.default_rng(31))
+    # rebuild the single copy from a known CI vector so both use the same state
+    dets1 = synth.ms0_determinants(na, nel)
+    ci1 = np.random.default_rng(77).standard_normal(len(dets1))
+    r1 = synth.reference_from_ci(na, nel, ci=ci1, dets=dets1)
+    for k in ("g1a", "g1b", "l2aa", "l2ab", "l2bb", "l3aaa", "l3aab", "l3abb", "l3bbb"):
+        inst[k] = r1[k]
+    e1 = _energies(inst)
+    # dimer: orbitals ordered [core A, core B, act A, act B, vir A, vir B]
+    n1 = nc + na + nv
+    eps = inst["eps"]
+    eps2 = np.concatenate([eps[:nc], eps[:nc], eps[nc:nc + na], eps[nc:nc + na], eps[nc + na:], eps[nc + na:]])
+    idxA = list(range(0, nc)) + list(range(2 * nc, 2 * nc + na)) + list(range(2 * nc + 2 * na, 2 * nc + 2 * na + nv))
+    idxB = list(range(nc, 2 * nc)) + list(range(2 * nc + na, 2 * nc + 2 * na)) + \
+        list(range(2 * nc + 2 * na + nv, 2 * (nc + na + nv)))
+    n2 = 2 * n1
+    B2 = np.zeros((2 * naux, n2, n2))
+    B2[np.ix_(range(naux), idxA, idxA)] = inst["B"]
+    B2[np.ix_(range(naux, 2 * naux), idxB, idxB)] = inst["B"]
+    dets, signs = product_dets_signs(dets1, na, dets1, na)
+    c1 = ci1 / np.linalg.norm(ci1)
+    ci2 = np.array([x * y for x in c1 for y in c1]) * signs
+    r2 = synth.reference_from_ci(2 * na, 2 * nel, ci=ci2, dets=dets)
+    dimer = dict(nc=2 * nc, na=2 * na, nv=2 * nv, naux=2 * naux, s=0.5, eps=eps2, B=B2)
+    for k in ("g1a", "g1b", "l2aa", "l2ab", "l2bb", "l3aaa", "l3aab", "l3abb", "l3bbb"):
+        dimer[k] = r2[k]
+    e2 = _energies(dimer)
+    assert np.allclose(e2, 2 * e1, rtol=1e-11, atol=1e-13)
+
+
+def test_density_fitting_equals_four_index():
+    """A full pivoted Cholesky of a PSD (pq|rs) gives B with identical
+    energies to the four-index integrals (Eq. int_fact with no truncation)."""
+    base = _small_mr(seed=10)
+    n = base["nc"] + base["na"] + base["nv"]
+    rng = np.random.default_rng(5)
+    B0 = rng.standard_normal((7, n, n))
+    B0 = 0.3 * (B0 + np.transpose(B0, (0, 2, 1)))
+    eri = np.einsum("Qpq,Qrs->pqrs", B0, B0)
+    M = eri.reshape(n * n, n * n).copy()
+    vecs = []
+    diag = np.diag(M).copy()
+    for _ in range(n * n):
+        k = int(np.argmax(diag))
+        if diag[k] < 1e-12:
+            break
+        col = M[:, k] - sum(v * v[k] for v in vecs) if vecs else M[:, k].copy()
+        L = col / np.sqrt(diag[k])
+        vecs.append(L)
+        diag -= L * L
+    Bc = np.array(vecs).reshape(len(vecs), n, n)
+    assert len(vecs) <= 7
+    e_df = _energies(dict(base, B=Bc, naux=len(vecs)))
+    r = dsrg.dsrg_pt3(dict(base, B=B0, naux=7), eri=eri)
+    e_4 = np.array([r["e2"], r["e3a"], r["e3b"]])
+    assert np.allclose(e_df, e_4, rtol=1e-11, atol=1e-13)
+
+
+def test_amplitude_symmetries():
+    """T2 antisymmetric, internal amplitudes zero, first-order T2 spin free
+    (t_aa = t_ab - t_ab with a,b exchanged)."""
+    inst = _small_mr(seed=11)
+    r = dsrg.dsrg_pt3(inst, return_intermediates=True)
+    P, I = r["_problem"], r["_inter"]
+    for key in ("T2", "T2b"):
+        T = I[key]
+        assert np.allclose(T, -np.transpose(T, (1, 0, 2, 3)))
+        assert np.allclose(T, -np.transpose(T, (0, 1, 3, 2)))
+        A = P.actm
+        assert np.abs(T[np.ix_(A, A, A, A)]).max() == 0.0
+    n = P.n
+    T = I["T2"]
+    aa = T[:n, :n, :n, :n]
+    ab = T[:n, n:, :n, n:]
+    assert np.allclose(aa, ab - np.transpose(ab, (1, 0, 2, 3)), atol=1e-15)
+    assert np.allclose(aa, T[n:, n:, n:, n:], atol=1e-15)
+
+
+def test_fock_offdiagonal_source_term():
+    """f^(1) enters T^(1)_1 linearly (Eq. T1_1st) and E(2) through
+    Htilde^(1)_1 (P. II.B explicit blocks); the oracle's E(2) with f^(1)
+    matches the Fock-space expectation value."""
+    inst, fs, psi, g, act, lam = mr_fock_instance(1, 2, 2, 1, 4, 0.5, seed=40)
+    n = inst["nc"] + inst["na"] + inst["nv"]
+    f1 = np.random.default_rng(2).standard_normal((n, n)) * 0.2
+    inst["f1"] = f1 + f1.T
+    r = dsrg.dsrg_pt3(inst, pt2_only=True, return_intermediates=True)
+    P, I = r["_problem"], r["_inter"]
+    NO = lambda Z, k: fsm.normal_ordered(fs, Z, k, g, act, lam)
+    H0 = NO(np.diag(P.eps), 1)
+    H1 = NO(P.V, 2) + NO(P.f1, 1)
+    Tm = NO(I["T1"], 1) + NO(I["T2"], 2)
+    Am = Tm - Tm.T
+    Ht1 = 2 * H1 + (H0 @ Am - Am @ H0)
+    E2 = psi @ (Ht1 @ Tm - Tm @ Ht1) @ psi
+    assert abs(E2 - r["e2"]) < 1e-12 * max(1, abs(E2))
+    assert np.abs(I["T1"]).max() > 1e-3
+
+
+@pytest.mark.slow
+def test_small_workload_runs():
+    inst = synth.config_instance("cas44_c2_v12_q60")
+    r = dsrg.dsrg_pt3(inst)
+    assert np.isfinite([r["e2"], r["e3"]]).all()
+    assert r["e2"] < 0

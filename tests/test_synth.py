@@ -1,0 +1,91 @@
+"""Pins of the input generator: density cumulants of the CAS reference.
+
+The method takes the reference only through gamma1, lambda2 and lambda3
+(Sec. II.A; Conclusions: at most the three-body cumulant is needed).  These
+checks fix the cumulant construction by properties that hold exactly.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fockspace as fsm
+
+from _fock_helpers import product_dets_signs
+
+
+def test_single_determinant_has_no_cumulants():
+    dets = synth.ms0_determinants(3, 4)
+    ci = np.zeros(len(dets))
+    ci[4] = 1.0
+    ref = synth.reference_from_ci(3, 4, ci=ci, dets=dets)
+    assert np.abs(ref["l2_so"]).max() < 1e-14
+    assert np.abs(ref["l3_so"]).max() < 1e-14
+    g = ref["g1_so"]
+    assert np.allclose(g @ g, g)  # idempotent
+
+
+def test_trace_and_partial_trace_identities():
+    rng = np.random.default_rng(4)
+    ref = synth.reference_from_ci(3, 4, rng=rng)
+    g, l2 = ref["g1_so"], ref["l2_so"]
+    assert abs(np.trace(g) - 4.0) < 1e-12
+    # sum_q G2[p,q,r,q] = (N-1) g[p,r]  =>  sum_q l2[p,q,r,q] = (g^2 - g)[p,r]
+    pt = np.einsum("pqrq->pr", l2)
+    assert np.allclose(pt, g @ g - g, atol=1e-13)
+    # Ms = 0: no alpha-beta block in gamma
+    na = 3
+    assert np.abs(g[:na, na:]).max() == 0.0
+
+
+def test_rdms_match_fock_space():
+    """Two independent constructions of the RDMs of the same state."""
+    rng = np.random.default_rng(9)
+    na, nel = 3, 2
+    dets = synth.ms0_determinants(na, nel)
+    ci = rng.standard_normal(len(dets))
+    ci /= np.linalg.norm(ci)
+    g1, G2, G3 = synth.rdms(2 * na, dets, ci, 3)
+    fs = fsm.FockSpace(2 * na, nel, kmax=3)
+    psi = fs.state(dets, ci)
+    assert np.allclose(fs.rdm(psi, 1), g1, atol=1e-14)
+    assert np.allclose(fs.rdm(psi, 2), G2, atol=1e-14)
+    assert np.allclose(fs.rdm(psi, 3), G3, atol=1e-14)
+
+
+def test_cumulants_are_additively_separable():
+    """A fermionic product of two states has no cumulant across the parts."""
+    rng = np.random.default_rng(2)
+    da = synth.ms0_determinants(2, 2)
+    db = synth.ms0_determinants(2, 2)
+    ca = rng.standard_normal(len(da))
+    cb = rng.standard_normal(len(db))
+    dets, signs = product_dets_signs(da, 2, db, 2)
+    ci = np.array([x * y for x in ca for y in cb]) * signs
+    ref = synth.reference_from_ci(4, 4, ci=ci, dets=dets)
+    l2, l3 = ref["l2_so"], ref["l3_so"]
+    # spin orbitals of part a: alpha 0,1 and beta 4,5; of part b: 2,3,6,7
+    A = [0, 1, 4, 5]
+    Bp = [2, 3, 6, 7]
+    mixed2 = 0.0
+    for idx in np.ndindex(*l2.shape):
+        parts = {x in A for x in idx}
+        if len(parts) > 1:
+            mixed2 = max(mixed2, abs(l2[idx]))
+    assert mixed2 < 1e-13
+    sub = np.ix_(*[A] * 6)
+    l3_mixed = l3.copy()
+    l3_mixed[sub] = 0.0
+    l3_mixed[np.ix_(*[Bp] * 6)] = 0.0
+    assert np.abs(l3_mixed).max() < 1e-13
+    # and within a part the cumulants are those of the part alone
+    ra = synth.reference_from_ci(2, 2, ci=ca, dets=da)
+    assert np.allclose(l3[np.ix_(*[A] * 6)], ra["l3_so"], atol=1e-13)
+    assert np.abs(ra["l3_so"]).max() > 1e-6 or np.abs(ra["l2_so"]).max() > 1e-3
+
+
+def test_instances_are_deterministic():
+    a = synth.config_instance("cas44_c2_v12_q60")
+    b = synth.config_instance("cas44_c2_v12_q60")
+    for k in ("eps", "B", "l3aab"):
+        assert np.array_equal(a[k], b[k])
+    assert np.allclose(a["B"], np.transpose(a["B"], (0, 2, 1)))
