@@ -163,13 +163,15 @@ class SpinOrbitalProblem:
         self.D2 = (e[None, None, :, None] + e[None, None, None, :]
                    - e[:, None, None, None] - e[None, :, None, None])  # D^{ij}_{ab} at [a,b,i,j]
 
-    # Eqs. T1_1st / T1_2nd: t^i_a = [f^i_a + sum_ux D^u_x t^{iu}_{ax} gamma^x_u] R(D^i_a)
+    # Eqs. T1_1st / T1_2nd: t^i_a = [f^i_a + sum_ux D^u_x t^{iu}_{ax} gamma^x_u] R(D^i_a).
+    # The paper's denominators put particle-type labels first:
+    # D^{ab..}_{ij..} = eps_i + eps_j + .. - eps_a - eps_b - .., so D^u_x = eps_x - eps_u.
     def amplitudes(self, f1_like, v_like):
         s = self.s
         T2 = np.where(self.mask2, v_like * regulariser(s, self.D2), 0.0)
         a = self.act
         e = self.eps
-        Dux = e[a][:, None] - e[a][None, :]             # D^u_x at [u, x]
+        Dux = e[a][None, :] - e[a][:, None]             # D^u_x = eps_x - eps_u at [u, x]
         g = self.gamma[np.ix_(a, a)]                    # gamma[x, u]
         T2ax = T2[:, :, :, a][:, a, :, :]               # T2[a, x, i, u] with x,u active
         src = np.einsum("axiu,ux,xu->ai", T2ax, Dux, g, optimize=True) if a.size else 0.0

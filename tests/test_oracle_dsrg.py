@@ -332,3 +332,38 @@ def test_small_workload_runs():
     r = dsrg.dsrg_pt3(inst)
     assert np.isfinite([r["e2"], r["e3"]]).all()
     assert r["e2"] < 0
+
+
+def test_first_order_htilde_matches_printed_blocks():
+    """Htilde^(1) = 2 H^(1) + [H^(0), A^(1)] evaluated by the (Fock-space
+    pinned) engine reproduces the paper's explicit non-diagonal blocks
+    (Sec. III): [Ht1]^i_a = f^i_a + [f^i_a + sum_ux D^u_x t^{iu}_{ax}
+    gamma^x_u] exp(-s (D^i_a)^2) and [Ht1]^{ij}_{ab} = v (1 + exp(-s D^2)).
+    This ties the amplitude formulas (Eqs. T1_1st, T2_1st) to the engine."""
+    inst, *_ = mr_fock_instance(1, 3, 2, 2, 6, 0.5, seed=44)
+    n = inst["nc"] + inst["na"] + inst["nv"]
+    f1 = np.random.default_rng(3).standard_normal((n, n)) * 0.1
+    inst["f1"] = f1 + f1.T
+    r = dsrg.dsrg_pt3(inst, pt2_only=True, return_intermediates=True)
+    P, I = r["_problem"], r["_inter"]
+    W = I["W"]
+    s = P.s
+    ph = P.mask1
+    Ht1_1 = 2 * P.f1 + W.z[1]
+    T1 = I["T1"]
+    R1 = dsrg.regulariser(s, P.D1)
+    e1 = np.exp(-s * P.D1 ** 2)
+    # the bracket [f + sum D t gamma] equals t / R where R != 0
+    bracket = np.where(np.abs(R1) > 1e-300, T1 / np.where(np.abs(R1) > 1e-300, R1, 1.0), 0.0)
+    printed_1 = P.f1 + bracket * e1
+    assert np.abs((Ht1_1 - printed_1)[ph]).max() < 1e-12
+    # and the bracket itself is the printed source term with D^u_x = eps_x - eps_u
+    a = P.act
+    e = P.eps
+    T2 = I["T2"]
+    src = np.einsum("axiu,ux,xu->ai", T2[:, :, :, a][:, a, :, :], e[a][None, :] - e[a][:, None],
+                    P.gamma[np.ix_(a, a)])
+    assert np.abs((bracket - (P.f1 + src))[ph]).max() < 1e-12
+    Ht1_2 = 2 * P.V + W.z[2]
+    printed_2 = P.V * (1 + np.exp(-s * P.D2 ** 2))
+    assert np.abs((Ht1_2 - printed_2)[P.mask2]).max() < 1e-12
