@@ -1,0 +1,137 @@
+/*
+ * dsrg.h -- C interface of the GB300 DSRG-MRPT2/PT3 energy library.
+ *
+ * Computes the unrelaxed second- and third-order energies of the driven
+ * similarity renormalization group perturbation theory (Li & Evangelista,
+ * "Driven similarity renormalization group: Third-order multireference
+ * perturbation theory"):
+ *   E(2) = <[Htilde(1), T(1)]>                          (Eq. E(2))
+ *   E(3) = <[Htilde(1), T(2)]> + <[Htilde(2)_{1,2}, T(1)]>  (Eq. E(3), with the
+ *          one- and two-body truncation of Htilde(2) stated after Eq. E(3))
+ * with first- and second-order amplitudes of Eqs. T1_1st, T2_1st, T1_2nd and
+ * T2_2nd (regulariser (1 - exp(-s D^2)) / D), H(0) the diagonal Fock blocks
+ * of Eq. F0th, and two-electron integrals from the factorisation
+ * (pq|rs) = sum_Q B^Q_pq B^Q_rs of Eq. int_fact.  The reference enters only
+ * through gamma1 and the two- and three-body density cumulants.  E(0) is not
+ * computed (it needs the bare one-electron integrals, which are not inputs).
+ *
+ * Orbitals are numbered core [0, nc), active [nc, nc+na), virtual
+ * [nc+na, n), n = nc + na + nv, all spin-free (restricted) quantities.
+ *
+ * Errors: every int-returning call gives 0 on success or a negative
+ * DSRG_ERR_* code; dsrg_last_error() then returns a message for the calling
+ * thread.  No call aborts the process.  All computation runs in the
+ * library's CUDA kernels on the current device; there is no CPU fallback.
+ */
+#ifndef DSRG_H
+#define DSRG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSRG_OK 0
+#define DSRG_ERR_ARG (-1)     /* invalid size, pointer or parameter          */
+#define DSRG_ERR_OOM (-2)     /* device allocation failed                    */
+#define DSRG_ERR_CUDA (-3)    /* CUDA runtime or launch error                */
+#define DSRG_ERR_STATE (-4)   /* call out of order (e.g. NULL handle)        */
+#define DSRG_ERR_INTERNAL (-5)
+
+#define DSRG_MEM_HOST 0   /* input pointers are host memory; copied at load     */
+#define DSRG_MEM_DEVICE 1 /* input pointers are device memory on the current GPU;
+                             copied at load as well                            */
+
+#define DSRG_PREC_FP64 0  /* every contraction in FP64                          */
+
+typedef struct dsrg_handle dsrg_handle;
+
+/*
+ * Problem inputs.  Row-major, FP64.  The caller keeps ownership; the
+ * library copies everything during dsrg_init / dsrg_load.
+ *   eps   [n]              semicanonical Fock diagonals (Eq. F0th)
+ *   B     [naux][n][n]     three-index factor, symmetric in its last two
+ *                          indices (Eq. int_fact)
+ *   g1a, g1b [na][na]      active one-particle density per spin,
+ *                          g1[u][v] = <a+_u a_v>
+ *   l2aa, l2ab, l2bb [na]^4  two-body cumulant spin blocks,
+ *                          l2xy[u][v][w][z] = lambda(a+_u a+_v a_z a_w) with
+ *                          the spins of (u,w) and (v,z) given by x and y
+ *   l3aaa, l3aab, l3abb, l3bbb [na]^6  three-body cumulant spin blocks,
+ *                          l3[u][v][w][x][y][z] is the cumulant of
+ *                          a+_u a+_v a+_w a_z a_y a_x; creators and
+ *                          annihilators in each slot position carry the
+ *                          spins named by the block (alpha first)
+ *   f1    [n][n] or NULL   off-diagonal Fock part f^(1) (its core-core,
+ *                          active-active and virtual-virtual blocks are
+ *                          ignored); NULL means zero
+ *   s                      flow parameter (> 0), in Eh^-2
+ */
+typedef struct {
+  int nc, na, nv, naux;
+  double s;
+  const double *eps;
+  const double *B;
+  const double *g1a, *g1b;
+  const double *l2aa, *l2ab, *l2bb;
+  const double *l3aaa, *l3aab, *l3abb, *l3bbb;
+  const double *f1;
+  int memory; /* DSRG_MEM_HOST or DSRG_MEM_DEVICE */
+} dsrg_inputs;
+
+typedef struct {
+  int precision;  /* DSRG_PREC_FP64 */
+  void *stream;   /* cudaStream_t to run on; NULL = the library's own stream */
+} dsrg_options;
+
+typedef struct {
+  double e2;   /* second-order energy E(2)                                  */
+  double e3a;  /* <[Htilde(1), T(2)]>                                        */
+  double e3b;  /* <[Htilde(2)_{1,2}, T(1)]>                                  */
+  double e3;   /* e3a + e3b                                                  */
+} dsrg_energies;
+
+/* Create a handle on the current CUDA device and load the inputs.  On
+ * success *out owns device memory until dsrg_free.  opts may be NULL. */
+int dsrg_init(const dsrg_inputs *in, const dsrg_options *opts, dsrg_handle **out);
+
+/* Replace the inputs of an existing handle with new ones of the same sizes
+ * (no reallocation of the input arrays). */
+int dsrg_load(dsrg_handle *h, const dsrg_inputs *in);
+
+/* E(2) only (fills e2; e3* set to 0). Synchronises the handle's stream. */
+int dsrg_pt2(dsrg_handle *h, dsrg_energies *out);
+
+/* E(2) and E(3) components.  Synchronises the handle's stream. */
+int dsrg_pt3(dsrg_handle *h, dsrg_energies *out);
+
+/* Release all device memory of the handle (NULL is ignored). */
+void dsrg_free(dsrg_handle *h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *dsrg_last_error(void);
+
+/* Number of this library's kernel launches issued by the last dsrg_pt2 /
+ * dsrg_pt3 call on the handle (-1 on a NULL handle). */
+long long dsrg_last_launch_count(const dsrg_handle *h);
+
+/* Peak device bytes held by the handle's tensor workspace. */
+long long dsrg_peak_bytes(const dsrg_handle *h);
+
+/*
+ * Intermediate access for testing.  Copies a named spin-orbital tensor of the
+ * last dsrg_pt2/dsrg_pt3 call to host memory `dst` (FP64, row-major) if its
+ * element count equals `count`.  Names and layouts, with H = core+active
+ * (h = nc+na) and P = active+virtual (p = na+nv), each slot spin-major
+ * (index sigma*len + x):
+ *   "T1" [2p][2h], "T2" [2p][2p][2h][2h]       first-order amplitudes
+ *   "T1b" [2p][2h], "T2b" [2p][2p][2h][2h]     second-order amplitudes
+ *   "O1" [2p][2h], "O2" [2p][2p][2h][2h]       excitation blocks of
+ *                                              1/2 [Htilde(1), A(1)]_{1,2}
+ * Returns DSRG_ERR_ARG for an unknown name or a wrong count.
+ */
+int dsrg_fetch(const dsrg_handle *h, const char *name, double *dst, long long count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSRG_H */

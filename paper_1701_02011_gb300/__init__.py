@@ -1,0 +1,218 @@
+"""Python binding of the GB300 DSRG-MRPT2/PT3 energy library (include/dsrg.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libdsrg.so``.  Importing works without a GPU; the first call
+that needs the library loads it and raises if it has not been built.
+
+Inputs are a dict with the keys of ``dsrg_inputs``: nc, na, nv, naux, s,
+eps, B, g1a, g1b, l2aa, l2ab, l2bb, l3aaa, l3aab, l3abb, l3bbb and optional
+f1.  Arrays may be numpy (host memory) or CUDA torch tensors (device memory,
+float64, contiguous); all arrays of one call must live in the same place.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libdsrg.so")
+
+DSRG_MEM_HOST = 0
+DSRG_MEM_DEVICE = 1
+DSRG_PREC_FP64 = 0
+
+_P = ctypes.POINTER(ctypes.c_double)
+
+
+class dsrg_inputs(ctypes.Structure):
+    _fields_ = [("nc", ctypes.c_int), ("na", ctypes.c_int), ("nv", ctypes.c_int), ("naux", ctypes.c_int),
+                ("s", ctypes.c_double), ("eps", _P), ("B", _P), ("g1a", _P), ("g1b", _P),
+                ("l2aa", _P), ("l2ab", _P), ("l2bb", _P), ("l3aaa", _P), ("l3aab", _P), ("l3abb", _P),
+                ("l3bbb", _P), ("f1", _P), ("memory", ctypes.c_int)]
+
+
+class dsrg_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class dsrg_energies(ctypes.Structure):
+    _fields_ = [("e2", ctypes.c_double), ("e3a", ctypes.c_double), ("e3b", ctypes.c_double),
+                ("e3", ctypes.c_double)]
+
+
+EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_free", "dsrg_last_error",
+           "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch")
+
+_lib = None
+
+
+def load_library(path: str = LIBPATH) -> ctypes.CDLL:
+    """Load libdsrg.so; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1701_02011_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    L.dsrg_init.argtypes = [ctypes.POINTER(dsrg_inputs), ctypes.POINTER(dsrg_options), ctypes.POINTER(ctypes.c_void_p)]
+    L.dsrg_init.restype = ctypes.c_int
+    L.dsrg_load.argtypes = [ctypes.c_void_p, ctypes.POINTER(dsrg_inputs)]
+    L.dsrg_load.restype = ctypes.c_int
+    for f in ("dsrg_pt2", "dsrg_pt3"):
+        getattr(L, f).argtypes = [ctypes.c_void_p, ctypes.POINTER(dsrg_energies)]
+        getattr(L, f).restype = ctypes.c_int
+    L.dsrg_free.argtypes = [ctypes.c_void_p]
+    L.dsrg_free.restype = None
+    L.dsrg_last_error.argtypes = []
+    L.dsrg_last_error.restype = ctypes.c_char_p
+    L.dsrg_last_launch_count.argtypes = [ctypes.c_void_p]
+    L.dsrg_last_launch_count.restype = ctypes.c_longlong
+    L.dsrg_peak_bytes.argtypes = [ctypes.c_void_p]
+    L.dsrg_peak_bytes.restype = ctypes.c_longlong
+    L.dsrg_fetch.argtypes = [ctypes.c_void_p, ctypes.c_char_p, _P, ctypes.c_longlong]
+    L.dsrg_fetch.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class DsrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dsrg error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != 0:
+        raise DsrgError(rc, load_library().dsrg_last_error().decode())
+
+
+_ARRAYS = ("eps", "B", "g1a", "g1b", "l2aa", "l2ab", "l2bb", "l3aaa", "l3aab", "l3abb", "l3bbb", "f1")
+
+
+def _pointer(x, keep, device):
+    if x is None:
+        return None
+    if device:
+        if not (x.is_cuda and x.dtype.is_floating_point and x.element_size() == 8 and x.is_contiguous()):
+            raise ValueError("device inputs must be contiguous float64 CUDA tensors")
+        keep.append(x)
+        return ctypes.cast(ctypes.c_void_p(x.data_ptr()), _P)
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    keep.append(a)
+    return a.ctypes.data_as(_P)
+
+
+def _is_device(inst):
+    for k in _ARRAYS:
+        x = inst.get(k)
+        if x is not None and hasattr(x, "is_cuda"):
+            return bool(x.is_cuda)
+    return False
+
+
+def make_inputs(inst: dict):
+    """Return (dsrg_inputs, keepalive list)."""
+    device = _is_device(inst)
+    keep = []
+    s = dsrg_inputs()
+    s.nc, s.na, s.nv, s.naux = int(inst["nc"]), int(inst["na"]), int(inst["nv"]), int(inst["naux"])
+    s.s = float(inst["s"])
+    for k in _ARRAYS:
+        p = _pointer(inst.get(k), keep, device)
+        setattr(s, k, p)
+    s.memory = DSRG_MEM_DEVICE if device else DSRG_MEM_HOST
+    return s, keep
+
+
+def dsrg_init(inst: dict, stream=None, precision=DSRG_PREC_FP64) -> ctypes.c_void_p:
+    L = load_library()
+    s, keep = make_inputs(inst)
+    opt = dsrg_options(precision, ctypes.c_void_p(stream) if stream else None)
+    h = ctypes.c_void_p()
+    _check(L.dsrg_init(ctypes.byref(s), ctypes.byref(opt), ctypes.byref(h)))
+    return h
+
+
+def dsrg_load(h, inst: dict) -> None:
+    s, keep = make_inputs(inst)
+    _check(load_library().dsrg_load(h, ctypes.byref(s)))
+
+
+def _energies(fn, h):
+    e = dsrg_energies()
+    _check(fn(h, ctypes.byref(e)))
+    return {"e2": e.e2, "e3a": e.e3a, "e3b": e.e3b, "e3": e.e3}
+
+
+def dsrg_pt2(h) -> dict:
+    return _energies(load_library().dsrg_pt2, h)
+
+
+def dsrg_pt3(h) -> dict:
+    return _energies(load_library().dsrg_pt3, h)
+
+
+def dsrg_free(h) -> None:
+    if h:
+        load_library().dsrg_free(h)
+
+
+def dsrg_last_launch_count(h) -> int:
+    return int(load_library().dsrg_last_launch_count(h))
+
+
+def dsrg_peak_bytes(h) -> int:
+    return int(load_library().dsrg_peak_bytes(h))
+
+
+def tensor_shape(name: str, nc: int, na: int, nv: int):
+    h, p = 2 * (nc + na), 2 * (na + nv)
+    if name in ("T1", "T1b", "O1"):
+        return (p, h)
+    if name in ("T2", "T2b", "O2"):
+        return (p, p, h, h)
+    raise KeyError(name)
+
+
+def dsrg_fetch(h, name: str, nc: int, na: int, nv: int) -> np.ndarray:
+    shape = tensor_shape(name, nc, na, nv)
+    out = np.empty(shape, dtype=np.float64)
+    _check(load_library().dsrg_fetch(h, name.encode(), out.ctypes.data_as(_P), int(out.size)))
+    return out
+
+
+class Dsrg:
+    """Convenience owner of one handle."""
+
+    def __init__(self, inst: dict, stream=None):
+        self.sizes = (int(inst["nc"]), int(inst["na"]), int(inst["nv"]))
+        self.h = dsrg_init(inst, stream)
+
+    def load(self, inst):
+        dsrg_load(self.h, inst)
+
+    def pt2(self):
+        return dsrg_pt2(self.h)
+
+    def pt3(self):
+        return dsrg_pt3(self.h)
+
+    def fetch(self, name):
+        return dsrg_fetch(self.h, name, *self.sizes)
+
+    @property
+    def launches(self):
+        return dsrg_last_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            dsrg_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,274 @@
+// C interface (include/dsrg.h) over the GPU energy driver.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "../../include/dsrg.h"
+#include "dsrg_impl.cuh"
+
+struct dsrg_handle {
+  dsrg::Handle* h;
+};
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int classify(const std::exception& e) {
+  std::string m = e.what();
+  if (m.find("cudaMalloc") != std::string::npos || m.find("out of memory") != std::string::npos)
+    return DSRG_ERR_OOM;
+  if (m.find("CUDA") != std::string::npos || m.find("cuda") != std::string::npos) return DSRG_ERR_CUDA;
+  return DSRG_ERR_INTERNAL;
+}
+
+size_t pow_na(int na, int k) {
+  size_t r = 1;
+  for (int i = 0; i < k; ++i) r *= (size_t)na;
+  return r;
+}
+
+int validate(const dsrg_inputs* in) {
+  if (!in) return fail(DSRG_ERR_ARG, "inputs are NULL");
+  if (in->nc < 0 || in->na < 0 || in->nv < 0 || in->naux < 1)
+    return fail(DSRG_ERR_ARG, "sizes must be nc, na, nv >= 0 and naux >= 1");
+  if (in->nc + in->na + in->nv < 1) return fail(DSRG_ERR_ARG, "no orbitals");
+  if (in->na > 16) return fail(DSRG_ERR_ARG, "at most 16 active orbitals are supported");
+  if (!(in->s > 0.0) || !std::isfinite(in->s)) return fail(DSRG_ERR_ARG, "flow parameter s must be positive");
+  if (!in->eps || !in->B) return fail(DSRG_ERR_ARG, "eps and B are required");
+  if (in->na > 0 && (!in->g1a || !in->g1b || !in->l2aa || !in->l2ab || !in->l2bb || !in->l3aaa || !in->l3aab ||
+                     !in->l3abb || !in->l3bbb))
+    return fail(DSRG_ERR_ARG, "active-space densities and cumulants are required when na > 0");
+  if (in->memory != DSRG_MEM_HOST && in->memory != DSRG_MEM_DEVICE) return fail(DSRG_ERR_ARG, "bad memory kind");
+  return DSRG_OK;
+}
+
+void copy_in(double* dst, const double* src, size_t n, int memory, cudaStream_t st) {
+  if (n == 0) return;
+  dsrg::check_cuda(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                                   memory == DSRG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st),
+                   "cudaMemcpyAsync (inputs)");
+}
+
+// copy the inputs and rebuild gamma, eta, cumulants and f1 on spin orbitals
+void load_inputs(dsrg::Handle& h, const dsrg_inputs* in) {
+  using namespace dsrg;
+  cudaStream_t st = h.stream;
+  const int n = h.n, na = h.na;
+  copy_in(h.eps, in->eps, (size_t)n, in->memory, st);
+  copy_in(h.B, in->B, (size_t)h.naux * n * n, in->memory, st);
+  const double* src[9] = {in->g1a, in->g1b, in->l2aa, in->l2ab, in->l2bb, in->l3aaa, in->l3aab, in->l3abb, in->l3bbb};
+  const int rank[9] = {2, 2, 4, 4, 4, 6, 6, 6, 6};
+  for (int k = 0; k < 9; ++k)
+    if (na > 0) copy_in(h.blk[k], src[k], pow_na(na, rank[k]), in->memory, st);
+  {
+    Iv hh[2] = {h.H, h.H}, pp[2] = {h.P, h.P};
+    h.gam = make_tensor(h.ws, 2, hh, false);
+    h.eta = make_tensor(h.ws, 2, pp, false);
+    launch_build_gamma_eta(h.nc, na, h.nv, h.blk[0], h.blk[1], h.gam.v.p, h.eta.v.p, st);
+    h.gam.v.mask = h.eta.v.mask = conserving_mask(2);
+  }
+  {
+    Iv a4[4] = {h.A, h.A, h.A, h.A}, a6[6] = {h.A, h.A, h.A, h.A, h.A, h.A};
+    h.L2 = make_tensor(h.ws, 4, a4, true);
+    h.L3 = make_tensor(h.ws, 6, a6, true);
+    if (na > 0) {
+      const double* b2[4] = {h.blk[2], h.blk[3], h.blk[4], nullptr};
+      const double* b3[4] = {h.blk[5], h.blk[6], h.blk[7], h.blk[8]};
+      launch_build_cumulant(na, 2, b2, h.L2.v.p, st);
+      launch_build_cumulant(na, 3, b3, h.L3.v.p, st);
+    }
+    h.L2.v.mask = conserving_mask(4);
+    h.L3.v.mask = conserving_mask(6);
+  }
+  h.has_f1 = in->f1 != nullptr;
+  if (h.has_f1) {
+    if (!h.f1raw) {
+      size_t cap;
+      h.f1raw = h.ws.get((size_t)n * n, cap);
+    }
+    copy_in(h.f1raw, in->f1, (size_t)n * n, in->memory, st);
+    // spin-orbital [G,G]: f1 on both spin diagonal blocks, its core-core,
+    // active-active and virtual-virtual parts removed (those are in H(0))
+    Iv gg[2] = {h.G, h.G};
+    h.F1 = make_tensor(h.ws, 2, gg, true);
+    const int lo[3] = {0, h.nc, h.nc + h.na}, hi[3] = {h.nc, h.nc + h.na, n};
+    for (int s = 0; s < 2; ++s)
+      for (int bi = 0; bi < 3; ++bi)
+        for (int bj = 0; bj < 3; ++bj) {
+          if (bi == bj) continue;
+          if (hi[bi] <= lo[bi] || hi[bj] <= lo[bj]) continue;
+          NdArgs g{};
+          g.nd = 2;
+          g.e[0] = hi[bi] - lo[bi];
+          g.e[1] = hi[bj] - lo[bj];
+          g.sa[0] = n;
+          g.sa[1] = 1;
+          g.sb[0] = h.F1.v.st[0];
+          g.sb[1] = h.F1.v.st[1];
+          g.total = (long long)g.e[0] * g.e[1];
+          launch_axpy(g, 1.0, h.f1raw + (long long)lo[bi] * n + lo[bj],
+                      h.F1.v.p + s * (h.F1.v.ss[0] + h.F1.v.ss[1]) + lo[bi] * h.F1.v.st[0] + lo[bj] * h.F1.v.st[1],
+                      st);
+        }
+    h.F1.v.mask = conserving_mask(2);
+  }
+  check_cuda(cudaGetLastError(), "launch (load)");
+}
+}  // namespace
+
+extern "C" {
+
+const char* dsrg_last_error(void) { return g_last_error.c_str(); }
+
+int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out) {
+  g_last_error.clear();
+  if (!out) return fail(DSRG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate(in);
+  if (rc) return rc;
+  if (opts && opts->precision != DSRG_PREC_FP64) return fail(DSRG_ERR_ARG, "unsupported precision");
+  cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+  bool own = false;
+  if (!st) {
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(DSRG_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    own = true;
+  }
+  dsrg::Handle* h = new (std::nothrow) dsrg::Handle(st);
+  if (!h) {
+    if (own) cudaStreamDestroy(st);
+    return fail(DSRG_ERR_OOM, "host allocation failed");
+  }
+  h->own_stream = own;
+  try {
+    h->nc = in->nc;
+    h->na = in->na;
+    h->nv = in->nv;
+    h->naux = in->naux;
+    h->n = in->nc + in->na + in->nv;
+    h->s = in->s;
+    h->C = {0, in->nc};
+    h->A = {in->nc, in->nc + in->na};
+    h->V = {in->nc + in->na, h->n};
+    h->H = {0, in->nc + in->na};
+    h->P = {in->nc, h->n};
+    h->G = {0, h->n};
+    size_t cap;
+    h->eps = h->ws.get((size_t)h->n, cap);
+    h->B = h->ws.get((size_t)h->naux * h->n * h->n, cap);
+    const int rank[9] = {2, 2, 4, 4, 4, 6, 6, 6, 6};
+    if (h->na > 0)
+      for (int k = 0; k < 9; ++k) h->blk[k] = h->ws.get(pow_na(h->na, rank[k]), cap);
+    h->ws.cap_results = 1 << 16;
+    dsrg::check_cuda(cudaMalloc(&h->ws.results, h->ws.cap_results * sizeof(double)), "cudaMalloc (results)");
+    h->ws.dot_scratch_len = 2 * 152 * 16;
+    dsrg::check_cuda(cudaMalloc(&h->ws.dot_scratch, h->ws.dot_scratch_len * sizeof(double)), "cudaMalloc (scratch)");
+    load_inputs(*h, in);
+    dsrg::check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize (init)");
+  } catch (const std::exception& e) {
+    int code = classify(e);
+    std::string msg = e.what();
+    delete h;
+    if (own) cudaStreamDestroy(st);
+    return fail(code, msg);
+  }
+  dsrg_handle* hd = new (std::nothrow) dsrg_handle{h};
+  if (!hd) {
+    delete h;
+    if (own) cudaStreamDestroy(st);
+    return fail(DSRG_ERR_OOM, "host allocation failed");
+  }
+  *out = hd;
+  return DSRG_OK;
+}
+
+int dsrg_load(dsrg_handle* hd, const dsrg_inputs* in) {
+  g_last_error.clear();
+  if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
+  int rc = validate(in);
+  if (rc) return rc;
+  dsrg::Handle& h = *hd->h;
+  if (in->nc != h.nc || in->na != h.na || in->nv != h.nv || in->naux != h.naux)
+    return fail(DSRG_ERR_ARG, "dsrg_load needs the sizes the handle was created with");
+  try {
+    h.s = in->s;
+    load_inputs(h, in);
+  } catch (const std::exception& e) {
+    return fail(classify(e), e.what());
+  }
+  return DSRG_OK;
+}
+
+static int run(dsrg_handle* hd, bool pt3, dsrg_energies* out) {
+  g_last_error.clear();
+  if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
+  if (!out) return fail(DSRG_ERR_ARG, "out is NULL");
+  try {
+    double e2 = 0, e3a = 0, e3b = 0;
+    dsrg::run_energy(*hd->h, pt3, &e2, &e3a, &e3b);
+    dsrg::check_cuda(cudaGetLastError(), "kernel launch");
+    dsrg::check_cuda(cudaStreamSynchronize(hd->h->stream), "cudaStreamSynchronize");
+    out->e2 = e2;
+    out->e3a = e3a;
+    out->e3b = e3b;
+    out->e3 = e3a + e3b;
+  } catch (const std::exception& e) {
+    return fail(classify(e), e.what());
+  }
+  return DSRG_OK;
+}
+
+int dsrg_pt2(dsrg_handle* hd, dsrg_energies* out) { return run(hd, false, out); }
+int dsrg_pt3(dsrg_handle* hd, dsrg_energies* out) { return run(hd, true, out); }
+
+void dsrg_free(dsrg_handle* hd) {
+  if (!hd) return;
+  if (hd->h) {
+    cudaStream_t st = hd->h->stream;
+    bool own = hd->h->own_stream;
+    cudaStreamSynchronize(st);
+    delete hd->h;
+    if (own) cudaStreamDestroy(st);
+  }
+  delete hd;
+}
+
+long long dsrg_last_launch_count(const dsrg_handle* hd) {
+  if (!hd || !hd->h) return -1;
+  return hd->h->launches;
+}
+
+long long dsrg_peak_bytes(const dsrg_handle* hd) {
+  if (!hd || !hd->h) return -1;
+  return (long long)hd->h->ws.peak_bytes();
+}
+
+int dsrg_fetch(const dsrg_handle* hd, const char* name, double* dst, long long count) {
+  g_last_error.clear();
+  if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
+  if (!name || !dst) return fail(DSRG_ERR_ARG, "name and dst are required");
+  const dsrg::Handle& h = *hd->h;
+  const dsrg::Tensor* t = nullptr;
+  if (!strcmp(name, "T1")) t = &h.T1;
+  else if (!strcmp(name, "T2")) t = &h.T2;
+  else if (!strcmp(name, "T1b")) t = &h.T1b;
+  else if (!strcmp(name, "T2b")) t = &h.T2b;
+  else if (!strcmp(name, "O1")) t = &h.O1;
+  else if (!strcmp(name, "O2")) t = &h.O2;
+  else return fail(DSRG_ERR_ARG, std::string("unknown tensor ") + name);
+  if (!t->v.p) return fail(DSRG_ERR_STATE, std::string(name) + " has not been computed");
+  if ((long long)t->n != count) return fail(DSRG_ERR_ARG, "element count mismatch");
+  cudaError_t e = cudaMemcpyAsync(dst, t->v.p, t->n * sizeof(double), cudaMemcpyDeviceToHost, h.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h.stream);
+  if (e != cudaSuccess) return fail(DSRG_ERR_CUDA, cudaGetErrorString(e));
+  return DSRG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,604 @@
+// DSRG-MRPT2/PT3 energy driver on the GPU (FP64 path).
+//
+// Term lists of the commutators [X, T] (X a Hermitian one- plus two-body
+// operator, T an excitation operator) in generalized normal order, derived
+// from the Mukherjee-Kutzelnigg Wick theorem (the paper defers them, Sec. III)
+// and written here by hand on spin orbitals with gamma, eta = 1 - gamma and
+// the two- and three-body cumulants.  Sums over hole (H) and particle (P)
+// ranges restrict themselves to the overlap where the ranges meet.
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+#include <vector>
+
+#include "dsrg_impl.cuh"
+
+namespace dsrg {
+
+namespace {
+Tensor mk(Handle& h, std::initializer_list<Iv> ivs, bool zero = true) {
+  std::vector<Iv> v(ivs);
+  return make_tensor(h.ws, (int)v.size(), v.data(), zero);
+}
+
+void raw_axpy4(Handle& h, double alpha, const double* src, const long long* ss, double* dst, const long long* ds,
+               const int* ext) {
+  NdArgs g{};
+  g.nd = 4;
+  g.total = 1;
+  for (int i = 0; i < 4; ++i) {
+    g.e[i] = ext[i];
+    g.sa[i] = ss[i];
+    g.sb[i] = ds[i];
+    g.total *= ext[i];
+  }
+  launch_axpy(g, alpha, src, dst, h.ws.stream);
+  h.ws.launches++;
+}
+
+// J[p,q,r,s] = sum_Q B[Q,p,r] B[Q,q,s] for p in I0, q in I1, r in I2, s in I3,
+// contiguous [L0][L1][L2][L3] (Eq. int_fact).
+void df_integrals(Handle& h, Iv I0, Iv I1, Iv I2, Iv I3, double* J) {
+  long long n = h.n;
+  int L1 = I1.len(), L2 = I2.len(), L3 = I3.len();
+  GemmArgs g{};
+  g.A = h.B + I0.lo * n + I2.lo;
+  g.B = h.B + I1.lo * n + I3.lo;
+  g.C = J;
+  g.alpha = 1.0;
+  g.nM = 2;
+  g.eM[0] = I0.len(); g.aM[0] = n; g.cM[0] = (long long)L1 * L2 * L3;
+  g.eM[1] = L2;       g.aM[1] = 1; g.cM[1] = L3;
+  g.nN = 2;
+  g.eN[0] = L1; g.bN[0] = n; g.cN[0] = (long long)L2 * L3;
+  g.eN[1] = L3; g.bN[1] = 1; g.cN[1] = 1;
+  g.nK = 1;
+  g.eK[0] = h.naux; g.aK[0] = n * n; g.bK[0] = n * n;
+  g.nB = 0;
+  g.M = (long long)I0.len() * L2;
+  g.N = (long long)L1 * L3;
+  g.K = h.naux;
+  g.nbatch = 1;
+  launch_gemm(g, h.ws.stream);
+  h.ws.launches++;
+}
+}  // namespace
+
+// <pq||rs> on a spin-orbital interval class, times coef.
+Tensor vclass(Handle& h, const Iv* ivs, double coef) {
+  Tensor V = make_tensor(h.ws, 4, ivs, true);
+  int L[4] = {ivs[0].len(), ivs[1].len(), ivs[2].len(), ivs[3].len()};
+  for (int k = 0; k < 4; ++k)
+    if (L[k] <= 0) return V;
+  size_t capJ, capK;
+  size_t nJ = (size_t)L[0] * L[1] * L[2] * L[3];
+  double* J = h.ws.get(nJ, capJ);
+  double* K = h.ws.get(nJ, capK);
+  check_cuda(cudaMemsetAsync(J, 0, nJ * sizeof(double), h.ws.stream), "memset");
+  check_cuda(cudaMemsetAsync(K, 0, nJ * sizeof(double), h.ws.stream), "memset");
+  df_integrals(h, ivs[0], ivs[1], ivs[2], ivs[3], J);  // (pr|qs) at [p,q,r,s]
+  df_integrals(h, ivs[0], ivs[1], ivs[3], ivs[2], K);  // (ps|qr) at [p,q,s,r]
+  long long sJ[4] = {(long long)L[1] * L[2] * L[3], (long long)L[2] * L[3], L[3], 1};
+  long long sK[4] = {(long long)L[1] * L[3] * L[2], (long long)L[3] * L[2], 1, L[2]};
+  const View& v = V.v;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double* dJ = v.p + a * v.ss[0] + b * v.ss[1] + a * v.ss[2] + b * v.ss[3];
+      raw_axpy4(h, coef, J, sJ, dJ, v.st, L);
+      double* dK = v.p + a * v.ss[0] + b * v.ss[1] + b * v.ss[2] + a * v.ss[3];
+      raw_axpy4(h, -coef, K, sK, dK, v.st, L);
+    }
+  V.v.mask = conserving_mask(4);
+  h.ws.put(J, capJ);
+  h.ws.put(K, capK);
+  return V;
+}
+
+// ---------------------------------------------------------------------------
+// operators X = c_v (f1 + V) + c_w W, with W given by its excitation blocks
+// ---------------------------------------------------------------------------
+void build_x(Handle& h, double c_v, const Tensor* W1, const Tensor* W2, double c_w, unsigned classes, Tensor& X1,
+             Sym2& X2) {
+  X1 = mk(h, {h.G, h.G});
+  if (c_v != 0.0 && h.has_f1) axpy(h.ws, c_v, h.F1.v, "pq", X1, "pq");
+  if (W1 && c_w != 0.0) {
+    axpy(h.ws, c_w, W1->v, "ai", X1, "ai");
+    axpy(h.ws, c_w, W1->v, "ai", X1, "ia");
+  }
+  X2.cls.clear();
+  const Iv& H = h.H;
+  const Iv& P = h.P;
+  Iv cl[5][4] = {{H, H, H, H}, {H, H, H, P}, {H, H, P, P}, {P, H, P, H}, {P, P, P, H}};
+  for (int c = 0; c < 5; ++c) {
+    if (!((classes >> c) & 1)) continue;
+    Tensor t = (c_v != 0.0) ? vclass(h, cl[c], c_v) : make_tensor(h.ws, 4, cl[c], true);
+    if (W2 && c_w != 0.0) {
+      axpy(h.ws, c_w, W2->v, "abcd", t, "abcd");
+      axpy(h.ws, c_w, W2->v, "cdab", t, "abcd");
+    }
+    X2.cls.push_back(std::move(t));
+  }
+}
+
+Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M) {
+  Iv ivs[kMaxRank];
+  for (int k = 0; k < X.v.rank; ++k) ivs[k] = X.v.iv[k];
+  ivs[slot] = isect(M.v.iv[0], X.v.iv[slot]);
+  Tensor out = make_tensor(h.ws, X.v.rank, ivs, true);
+  char lx[8], lo[8], lm[3];
+  for (int k = 0; k < X.v.rank; ++k) lx[k] = lo[k] = "abcdef"[k];
+  lx[X.v.rank] = lo[X.v.rank] = 0;
+  lo[slot] = 'z';
+  lm[0] = 'z';
+  lm[1] = lx[slot];
+  lm[2] = 0;
+  contract(h.ws, 1.0, M.v, lm, X.v, lx, out, lo);
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// amplitudes (Eqs. T1_1st, T2_1st, T1_2nd, T2_2nd) and [H0, A] (closed form)
+// ---------------------------------------------------------------------------
+// S[a,i] = sum_{x,u active} T2[a,x,i,u] gamma[x,u] (eps_x - eps_u)
+static Tensor gamma_source(Handle& h, const Tensor& T2) {
+  Tensor S = mk(h, {h.P, h.H});
+  if (h.na > 0) {
+    Tensor G = mk(h, {h.A, h.A}, false);
+    launch_gamma_delta(h.nc, h.na, h.eps, h.gam.v.p, h.nc + h.na, G.v.p, h.ws.stream);
+    h.ws.launches++;
+    G.v.mask = conserving_mask(2);
+    contract(h.ws, 1.0, T2.v, "axiu", G.v, "xu", S, "ai");
+  }
+  S.v.mask = conserving_mask(2);
+  return S;
+}
+
+void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tensor& T2, Tensor& W1, Tensor& W2) {
+  T2 = mk(h, {h.P, h.P, h.H, h.H}, false);
+  W2 = mk(h, {h.P, h.P, h.H, h.H}, false);
+  launch_amp2(h.nc, h.na, h.nv, h.s, h.eps, O2.v.p, T2.v.p, W2.v.p, h.ws.stream);
+  h.ws.launches++;
+  T2.v.mask = W2.v.mask = conserving_mask(4);
+  Tensor S = gamma_source(h, T2);
+  T1 = mk(h, {h.P, h.H}, false);
+  W1 = mk(h, {h.P, h.H}, false);
+  launch_amp1(h.nc, h.na, h.nv, h.s, h.eps, O1 ? O1->v.p : nullptr, S.v.p, T1.v.p, W1.v.p, h.ws.stream);
+  h.ws.launches++;
+  T1.v.mask = W1.v.mask = conserving_mask(2);
+}
+
+// ---------------------------------------------------------------------------
+// spin-free particle-particle ladder with (pr|qs) built from B in batches
+// ---------------------------------------------------------------------------
+// L[p,q,i,j] = sum_{r,s in P} (pr|qs) t[r,s,i,j] with t the alpha-beta block of
+// a spin-free T2 (first order, Eq. T2_1st); the spin blocks of
+// 1/2 sum_rs <pq||rs> T2[r,s,i,j] follow from L (Eq. scaling_problem).
+void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
+  const int p = h.na + h.nv, hh = h.nc + h.na;
+  const long long n = h.n;
+  if (p == 0 || hh == 0) return;
+  const View& tv = T2.v;
+  const double* t = tv.p + tv.ss[1] + tv.ss[3];
+  size_t capL;
+  size_t nL = (size_t)p * p * hh * hh;
+  double* L = h.ws.get(nL, capL);
+  check_cuda(cudaMemsetAsync(L, 0, nL * sizeof(double), h.ws.stream), "memset");
+  const long long p3 = (long long)p * p * p;
+  long long bp = (1LL << 27) / (p3 > 0 ? p3 : 1);  // <= 1 GiB of (pr|qs) per batch
+  if (bp < 1) bp = 1;
+  if (bp > p) bp = p;
+  size_t capG;
+  double* G = h.ws.get((size_t)(bp * p3), capG);
+  for (long long p0 = 0; p0 < p; p0 += bp) {
+    long long nb = (p - p0 < bp) ? p - p0 : bp;
+    check_cuda(cudaMemsetAsync(G, 0, (size_t)(nb * p3) * sizeof(double), h.ws.stream), "memset");
+    {  // G[pp,q,r,s] = sum_Q B[Q,P0+p0+pp,P0+r] B[Q,P0+q,P0+s]
+      GemmArgs g{};
+      g.A = h.B + (h.nc + p0) * n + h.nc;
+      g.B = h.B + h.nc * n + h.nc;
+      g.C = G;
+      g.alpha = 1.0;
+      g.nM = 2;
+      g.eM[0] = (int)nb; g.aM[0] = n; g.cM[0] = p3;
+      g.eM[1] = p;       g.aM[1] = 1; g.cM[1] = p;
+      g.nN = 2;
+      g.eN[0] = p; g.bN[0] = n; g.cN[0] = (long long)p * p;
+      g.eN[1] = p; g.bN[1] = 1; g.cN[1] = 1;
+      g.nK = 1;
+      g.eK[0] = h.naux; g.aK[0] = n * n; g.bK[0] = n * n;
+      g.M = nb * p;
+      g.N = (long long)p * p;
+      g.K = h.naux;
+      g.nbatch = 1;
+      launch_gemm(g, h.ws.stream);
+      h.ws.launches++;
+    }
+    {  // L[p0+pp,q,i,j] += sum_{r,s} G[pp,q,r,s] t[r,s,i,j]
+      GemmArgs g{};
+      g.A = G;
+      g.B = t;
+      g.C = L + p0 * (long long)p * hh * hh;
+      g.alpha = 1.0;
+      g.nM = 2;
+      g.eM[0] = (int)nb; g.aM[0] = p3;              g.cM[0] = (long long)p * hh * hh;
+      g.eM[1] = p;       g.aM[1] = (long long)p * p; g.cM[1] = (long long)hh * hh;
+      g.nK = 2;
+      g.eK[0] = p; g.aK[0] = p; g.bK[0] = tv.st[0];
+      g.eK[1] = p; g.aK[1] = 1; g.bK[1] = tv.st[1];
+      g.nN = 2;
+      g.eN[0] = hh; g.bN[0] = tv.st[2]; g.cN[0] = hh;
+      g.eN[1] = hh; g.bN[1] = tv.st[3]; g.cN[1] = 1;
+      g.M = nb * p;
+      g.N = (long long)hh * hh;
+      g.K = (long long)p * p;
+      g.nbatch = 1;
+      launch_gemm(g, h.ws.stream);
+      h.ws.launches++;
+    }
+  }
+  h.ws.put(G, capG);
+  // scatter into the spin blocks of C2 [2p][2p][2h][2h]
+  const View& c = C2.v;
+  int ext[4] = {p, p, hh, hh};
+  long long sL[4] = {(long long)p * hh * hh, (long long)hh * hh, hh, 1};
+  long long sLji[4] = {sL[0], sL[1], 1, hh};      // L[p,q,j,i]
+  long long sLqp[4] = {sL[1], sL[0], hh, 1};      // L[q,p,i,j]
+  auto blk = [&](int a, int b, int i, int j) { return c.p + a * c.ss[0] + b * c.ss[1] + i * c.ss[2] + j * c.ss[3]; };
+  raw_axpy4(h, coef, L, sL, blk(0, 1, 0, 1), c.st, ext);
+  raw_axpy4(h, coef, L, sL, blk(1, 0, 1, 0), c.st, ext);
+  raw_axpy4(h, -coef, L, sLji, blk(0, 1, 1, 0), c.st, ext);
+  raw_axpy4(h, -coef, L, sLji, blk(1, 0, 0, 1), c.st, ext);
+  for (int s = 0; s < 2; ++s) {
+    raw_axpy4(h, coef, L, sL, blk(s, s, s, s), c.st, ext);
+    raw_axpy4(h, -coef, L, sLqp, blk(s, s, s, s), c.st, ext);
+  }
+  C2.v.mask |= conserving_mask(4);
+  h.ws.put(L, capL);
+}
+
+// ---------------------------------------------------------------------------
+// [X, T] into one output block pair (C1, C2)
+// ---------------------------------------------------------------------------
+void commutator(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
+                Tensor& C2, bool df, const Tensor* Wpp, double c_wpp) {
+  Workspace& ws = h.ws;
+  const Tensor& g = h.gam;
+  const Tensor& e = h.eta;
+  const Tensor& L2 = h.L2;
+  const Iv& G = h.G;
+  const Iv& H = h.H;
+  const Iv& P = h.P;
+  const Iv& A = h.A;
+  const bool exc = (C2.v.iv[0].lo == P.lo && C2.v.iv[0].hi == P.hi);
+  // [X1, T1] one-body: X1 T1 - T1 X1
+  contract(ws, 1.0, X1.v, "pr", T1.v, "rq", C1, "pq");
+  contract(ws, -1.0, T1.v, "pr", X1.v, "rq", C1, "pq");
+  // [X1, T2] one-body: (gamma X1 eta - eta X1 gamma)[i,a] T2[a,b,i,j]
+  {
+    Tensor M1 = mk(h, {G, G});
+    Tensor t1 = mk(h, {G, P});
+    contract(ws, 1.0, X1.v, "pq", e.v, "qa", t1, "pa");
+    contract(ws, 1.0, g.v, "ip", t1.v, "pa", M1, "ia");
+    Tensor t2 = mk(h, {G, H});
+    contract(ws, 1.0, X1.v, "pq", g.v, "qa", t2, "pa");
+    contract(ws, -1.0, e.v, "ip", t2.v, "pa", M1, "ia");
+    contract(ws, 1.0, M1.v, "ia", T2.v, "abij", C1, "bj");
+  }
+  // [X1, T2] two-body
+  contract(ws, 1.0, X1.v, "xa", T2.v, "ayij", C2, "xyij");
+  contract(ws, -1.0, X1.v, "ya", T2.v, "axij", C2, "xyij");
+  contract(ws, -1.0, T2.v, "xyik", X1.v, "kj", C2, "xyij");
+  contract(ws, 1.0, T2.v, "xyjk", X1.v, "ki", C2, "xyij");
+  // [X2, T1] one-body: X2[p,q,s,r] (gamma T1^T eta)[q,r]
+  {
+    Tensor tmp = mk(h, {H, P});
+    contract(ws, 1.0, g.v, "qi", T1.v, "ai", tmp, "qa");
+    Tensor Mq = mk(h, {H, P});
+    contract(ws, 1.0, tmp.v, "qa", e.v, "ra", Mq, "qr");
+    contract_x2(ws, 1.0, X2, "pqsr", Mq.v, "qr", C1, "ps");
+  }
+  // [X2, T1] two-body
+  contract_x2(ws, 1.0, X2, "pqas", T1.v, "ar", C2, "pqrs");
+  contract_x2(ws, -1.0, X2, "pqar", T1.v, "as", C2, "pqrs");
+  contract_x2(ws, 1.0, X2, "qirs", T1.v, "pi", C2, "pqrs");
+  contract_x2(ws, -1.0, X2, "pirs", T1.v, "qi", C2, "pqrs");
+  // [X2, T2] one-body with three single contractions
+  Tensor Dee = dress(h, dress(h, T2, 0, e), 1, e);
+  Tensor Ehh = dress(h, dress(h, T2, 2, g), 3, g);
+  Tensor Nhh = dress(h, dress(h, T2, 2, e), 3, e);
+  {
+    Tensor D1 = dress(h, Dee, 2, g);
+    contract_x2(ws, -0.5, X2, "pqrs", D1.v, "rsqj", C1, "pj");
+    Tensor Dgg = dress(h, dress(h, T2, 0, g), 1, g);
+    Tensor D2 = dress(h, Dgg, 2, e);
+    contract_x2(ws, -0.5, X2, "pqrs", D2.v, "rsqj", C1, "pj");
+    Tensor D3 = dress(h, Ehh, 0, e);
+    contract_x2(ws, -0.5, X2, "pqrs", D3.v, "rbpq", C1, "bs");
+    Tensor D4 = dress(h, Nhh, 0, g);
+    contract_x2(ws, -0.5, X2, "pqrs", D4.v, "rbpq", C1, "bs");
+  }
+  // [X2, T2] one-body with a two-body cumulant
+  if (h.na > 0) {
+    {
+      Tensor Y = mk(h, {P, A});
+      contract(ws, 1.0, T2.v, "abij", L2.v, "qbij", Y, "aq");
+      Tensor Z = dress(h, Y, 0, e);
+      contract_x2(ws, -0.5, X2, "pqrs", Z.v, "rq", C1, "ps");
+    }
+    {
+      Tensor Y = mk(h, {H, A});
+      contract(ws, 1.0, T2.v, "abij", L2.v, "abjr", Y, "ir");
+      Tensor Z = dress(h, Y, 0, g);
+      contract_x2(ws, -0.5, X2, "pqrs", Z.v, "qr", C1, "ps");
+    }
+    {
+      Tensor Y = mk(h, {P, H, A, A});
+      contract(ws, 1.0, T2.v, "abij", L2.v, "qbjs", Y, "aiqs");
+      contract_x2(ws, -1.0, X2, "pqas", Y.v, "aiqs", C1, "pi");
+    }
+    {
+      Tensor Y = mk(h, {P, P, A, A});
+      contract(ws, 1.0, T2.v, "abij", L2.v, "pqij", Y, "abpq");
+      contract_x2(ws, -0.25, X2, "pqas", Y.v, "abpq", C1, "bs");
+    }
+    {
+      Tensor Y = mk(h, {P, A});
+      contract_x2(ws, 1.0, X2, "pqas", L2.v, "pqjs", Y, "aj");
+      contract(ws, -0.5, Y.v, "aj", T2.v, "abij", C1, "bi");
+    }
+    {
+      Tensor Y = mk(h, {C1.v.iv[0], H, A, A});
+      contract_x2(ws, 1.0, X2, "pirs", L2.v, "abrs", Y, "piab");
+      contract(ws, -0.25, Y.v, "piab", T2.v, "abij", C1, "pj");
+    }
+    {
+      Tensor Y = mk(h, {P, H, A, A});
+      contract(ws, 1.0, T2.v, "abij", L2.v, "pajr", Y, "bipr");
+      contract_x2(ws, -1.0, X2, "pirs", Y.v, "bipr", C1, "bs");
+    }
+    {
+      Tensor Y = mk(h, {H, A});
+      contract_x2(ws, 1.0, X2, "pirs", L2.v, "pars", Y, "ia");
+      contract(ws, -0.5, Y.v, "ia", T2.v, "abij", C1, "bj");
+    }
+  }
+  // [X2, T2] two-body: particle ladder 1/2 X2 T2 - X2[p,q,r,b] (gamma T2)[r,b,i,j]
+  if (exc) {
+    if (df) df_ladder(h, T2, C2, 1.0);
+    if (Wpp && c_wpp != 0.0 && h.na > 0) {
+      // W's particle-particle block lives on [P,P,A,A] and its transpose
+      const Iv ppaa[4] = {P, P, A, A};
+      View wv = Wpp->v.sub(ppaa);
+      contract(ws, 0.5 * c_wpp, wv, "pqrs", T2.v, "rsij", C2, "pqij");
+      contract(ws, 0.5 * c_wpp, wv, "rspq", T2.v, "rsij", C2, "pqij");
+    }
+  } else {
+    contract_x2(ws, 0.5, X2, "pqrs", T2.v, "rsij", C2, "pqij");
+  }
+  {
+    Tensor gT2 = dress(h, T2, 0, g);
+    contract_x2(ws, -1.0, X2, "pqrb", gT2.v, "rbij", C2, "pqij");
+  }
+  // hole ladder
+  contract_x2(ws, 0.5, X2, "pqrs", Ehh.v, "abpq", C2, "abrs");
+  contract_x2(ws, -0.5, X2, "pqrs", Nhh.v, "abpq", C2, "abrs");
+  // ring: K[x,y,u,w] = sum_{i,a} (Xbar - Xtilde)[x,i,a,w] T2[a,y,i,u], antisymmetrised
+  {
+    Iv xi = exc ? P : H, wi = exc ? H : P;
+    Iv want[4] = {xi, H, P, wi};
+    View xv;
+    double sg;
+    if (!X2.resolve(want, xv, sg)) throw std::runtime_error("ring: two-body class missing");
+    Tensor Xs = make_tensor(ws, 4, want, true);
+    axpy(ws, sg, xv, "abcd", Xs, "abcd");
+    Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
+    Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
+    Iv kiv[4] = {xi, P, H, wi};
+    Tensor K = make_tensor(ws, 4, kiv, true);
+    contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+    contract(ws, -1.0, Xt.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+    axpy(ws, 1.0, K.v, "xyuw", C2, "xyuw");
+    axpy(ws, -1.0, K.v, "xyuw", C2, "yxuw");
+    axpy(ws, -1.0, K.v, "xyuw", C2, "xywu");
+    axpy(ws, 1.0, K.v, "xyuw", C2, "yxwu");
+  }
+}
+
+// excitation blocks of [X, T - T^+] = [X, T] + [X, T]^+ (X Hermitian)
+void commutator_A(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
+                  Tensor& O2, bool df, const Tensor* Wpp, double c_wpp) {
+  Tensor C1e = mk(h, {h.P, h.H}), C1d = mk(h, {h.H, h.P});
+  Tensor C2e = mk(h, {h.P, h.P, h.H, h.H}), C2d = mk(h, {h.H, h.H, h.P, h.P});
+  commutator(h, X1, X2, T1, T2, C1e, C2e, df, Wpp, c_wpp);
+  commutator(h, X1, X2, T1, T2, C1d, C2d, df, Wpp, c_wpp);
+  O1 = mk(h, {h.P, h.H});
+  O2 = mk(h, {h.P, h.P, h.H, h.H});
+  axpy(h.ws, 1.0, C1e.v, "ai", O1, "ai");
+  axpy(h.ws, 1.0, C1d.v, "ia", O1, "ai");
+  axpy(h.ws, 1.0, C2e.v, "abij", O2, "abij");
+  axpy(h.ws, 1.0, C2d.v, "ijab", O2, "abij");
+}
+
+// ---------------------------------------------------------------------------
+// scalar <[X, T]>: only the X1[H,P] and X2[H,H,P,P] elements enter
+// ---------------------------------------------------------------------------
+void scalar(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2) {
+  Workspace& ws = h.ws;
+  const Tensor& g = h.gam;
+  const Tensor& e = h.eta;
+  const Iv& G = h.G;
+  const Iv& H = h.H;
+  const Iv& P = h.P;
+  const Iv& A = h.A;
+  {  // [X1, T1]
+    Tensor t2 = mk(h, {H, G});
+    contract(ws, 1.0, g.v, "ip", X1.v, "pq", t2, "iq");
+    Tensor tmp = mk(h, {H, P});
+    contract(ws, 1.0, t2.v, "iq", e.v, "qa", tmp, "ia");
+    dot(ws, 1.0, T1.v, "ai", tmp.v, "ia");
+  }
+  if (h.na > 0) {
+    const Tensor& L2 = h.L2;
+    {  // [X1, T2]
+      Tensor Y = mk(h, {P, A});
+      contract(ws, 1.0, T2.v, "abij", L2.v, "pbij", Y, "ap");
+      Tensor xe = mk(h, {A, P});
+      contract(ws, 1.0, X1.v, "pq", e.v, "qa", xe, "pa");
+      dot(ws, 0.5, xe.v, "pa", Y.v, "ap");
+      Tensor Z = mk(h, {H, A});
+      contract(ws, 1.0, T2.v, "abij", L2.v, "abjq", Z, "iq");
+      Tensor gx = mk(h, {H, A});
+      contract(ws, 1.0, g.v, "ip", X1.v, "pq", gx, "iq");
+      dot(ws, 0.5, gx.v, "iq", Z.v, "iq");
+    }
+    {  // [X2, T1]
+      Tensor Y = dress(h, T1, 0, e);
+      Tensor U = mk(h, {A, A, P, A});
+      contract(ws, 1.0, Y.v, "ri", L2.v, "pqis", U, "pqrs");
+      dot_x2(ws, 0.5, X2, U);
+      Tensor Y2 = mk(h, {H, P});
+      contract(ws, 1.0, g.v, "qi", T1.v, "ai", Y2, "qa");
+      Tensor U2 = mk(h, {A, H, A, A});
+      contract(ws, 1.0, Y2.v, "qa", L2.v, "pars", U2, "pqrs");
+      dot_x2(ws, -0.5, X2, U2);
+    }
+  }
+  // [X2, T2]
+  Tensor Dee = dress(h, dress(h, T2, 0, e), 1, e);
+  {
+    Tensor D = dress(h, dress(h, Dee, 2, g), 3, g);
+    Iv t[4] = {H, H, P, P};
+    Tensor Dt = make_tensor(ws, 4, t, true);
+    axpy(ws, 1.0, D.v, "rspq", Dt, "pqrs");
+    dot_x2(ws, 0.25, X2, Dt);
+  }
+  if (h.na > 0) {
+    const Tensor& L2 = h.L2;
+    const Tensor& L3 = h.L3;
+    {
+      Tensor U = mk(h, {A, A, P, P});
+      contract(ws, 1.0, Dee.v, "rsij", L2.v, "pqij", U, "pqrs");
+      dot_x2(ws, 0.125, X2, U);
+    }
+    {
+      Tensor Dgg = dress(h, dress(h, T2, 2, g), 3, g);
+      Tensor U = mk(h, {H, H, A, A});
+      contract(ws, 1.0, Dgg.v, "abpq", L2.v, "abrs", U, "pqrs");
+      dot_x2(ws, 0.125, X2, U);
+    }
+    {
+      Tensor Dp = dress(h, dress(h, T2, 0, e), 2, g);
+      Tensor U = mk(h, {A, H, P, A});
+      contract(ws, 1.0, Dp.v, "rbqj", L2.v, "pbjs", U, "pqrs");
+      dot_x2(ws, 1.0, X2, U);
+    }
+    {
+      Tensor De = dress(h, T2, 0, e);
+      Tensor U = mk(h, {A, A, P, A});
+      contract(ws, 1.0, De.v, "rbij", L3.v, "pqbijs", U, "pqrs");
+      dot_x2(ws, -0.25, X2, U);
+    }
+    {
+      Tensor Dg = dress(h, T2, 2, g);
+      Tensor U = mk(h, {A, H, A, A});
+      contract(ws, 1.0, Dg.v, "abqj", L3.v, "pabjrs", U, "pqrs");
+      dot_x2(ws, -0.25, X2, U);
+    }
+  }
+}
+
+// sum of the device result slots [lo, hi) (compensated, on the host)
+static double sum_results(Handle& h, int lo, int hi) {
+  if (hi <= lo) return 0.0;
+  std::vector<double> v(hi - lo);
+  check_cuda(cudaMemcpyAsync(v.data(), h.ws.results + lo, (hi - lo) * sizeof(double), cudaMemcpyDeviceToHost,
+                             h.ws.stream),
+             "copy results");
+  check_cuda(cudaStreamSynchronize(h.ws.stream), "sync");
+  long double s = 0.0L;
+  for (double x : v) s += x;
+  return (double)s;
+}
+
+// ---------------------------------------------------------------------------
+// the energy (Sec. II.B)
+// ---------------------------------------------------------------------------
+void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
+  Workspace& ws = h.ws;
+  ws.launches = 0;
+  ws.nresults = 0;
+  const Iv& H = h.H;
+  const Iv& P = h.P;
+  // first-order amplitudes from the non-diagonal part of H(1)
+  Tensor F1ph = mk(h, {P, H});
+  if (h.has_f1) axpy(ws, 1.0, h.F1.v, "ai", F1ph, "ai");
+  Tensor Vph;
+  {
+    Iv cl[4] = {P, P, H, H};
+    Vph = vclass(h, cl, 1.0);
+  }
+  Tensor T1, T2, W1, W2;
+  amplitudes(h, &F1ph, Vph, T1, T2, W1, W2);
+  Vph.release();
+  // Htilde(1) = 2 H(1) + [H(0), A(1)] (Eq. Hbar_1st): E(2) needs its H,H,P,P class only
+  Tensor Xs1;
+  Sym2 Xs2;
+  build_x(h, 2.0, &W1, &W2, 1.0, 1u << 2, Xs1, Xs2);
+  int r0 = ws.nresults;
+  scalar(h, Xs1, Xs2, T1, T2);
+  int r1 = ws.nresults;
+  *e2 = sum_results(h, r0, r1);
+  h.T1 = std::move(T1);
+  h.T2 = std::move(T2);
+  if (!pt3) {
+    *e3a = *e3b = 0.0;
+    h.launches = ws.launches;
+    return;
+  }
+  const Tensor& t1 = h.T1;
+  const Tensor& t2 = h.T2;
+  // O = 1/2 [Htilde(1), A(1)]_{1,2} = [H(1) + W/2, A(1)]_{1,2}
+  Tensor X1;
+  Sym2 X2;
+  build_x(h, 1.0, &W1, &W2, 0.5, 0x1f, X1, X2);
+  Tensor O1, O2;
+  commutator_A(h, X1, X2, t1, t2, O1, O2, true, &W2, 0.5);
+  X2.cls.clear();
+  X1.release();
+  // second-order amplitudes (Eqs. T1_2nd, T2_2nd) and [H(0), A(2)]
+  Tensor U1, U2, V1, V2;
+  amplitudes(h, &O1, O2, U1, U2, V1, V2);
+  // [W, A(1)]_{1,2}
+  Tensor Y1;
+  Sym2 Y2;
+  build_x(h, 0.0, &W1, &W2, 1.0, 0x1f, Y1, Y2);
+  Tensor Q1, Q2;
+  commutator_A(h, Y1, Y2, t1, t2, Q1, Q2, false, &W2, 1.0);
+  Y2.cls.clear();
+  Y1.release();
+  // Htilde(2)_{1,2} excitation blocks = [H0, A(2)] + O - [W, A(1)] / 6
+  Tensor Z1 = mk(h, {P, H}), Z2 = mk(h, {P, P, H, H});
+  axpy(ws, 1.0, V1.v, "ai", Z1, "ai");
+  axpy(ws, 1.0, O1.v, "ai", Z1, "ai");
+  axpy(ws, -1.0 / 6.0, Q1.v, "ai", Z1, "ai");
+  axpy(ws, 1.0, V2.v, "abij", Z2, "abij");
+  axpy(ws, 1.0, O2.v, "abij", Z2, "abij");
+  axpy(ws, -1.0 / 6.0, Q2.v, "abij", Z2, "abij");
+  Tensor Zx1;
+  Sym2 Zx2;
+  build_x(h, 0.0, &Z1, &Z2, 1.0, 1u << 2, Zx1, Zx2);
+  int r2 = ws.nresults;
+  scalar(h, Xs1, Xs2, U1, U2);
+  int r3 = ws.nresults;
+  scalar(h, Zx1, Zx2, t1, t2);
+  int r4 = ws.nresults;
+  *e3a = sum_results(h, r2, r3);
+  *e3b = sum_results(h, r3, r4);
+  h.T1b = std::move(U1);
+  h.T2b = std::move(U2);
+  h.O1 = std::move(O1);
+  h.O2 = std::move(O2);
+  h.launches = ws.launches;
+}
+
+}  // namespace dsrg

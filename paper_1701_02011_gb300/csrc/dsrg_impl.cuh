@@ -1,0 +1,41 @@
+// Internal state of a DSRG energy handle.
+#pragma once
+#include "engine.cuh"
+
+namespace dsrg {
+
+struct Handle {
+  int nc = 0, na = 0, nv = 0, n = 0, naux = 0;
+  double s = 0.0;
+  Iv C, A, V, H, P, G;  // core, active, virtual, hole, particle, general
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Workspace ws;
+  // inputs (device)
+  double* eps = nullptr;
+  double* B = nullptr;
+  double* f1raw = nullptr;
+  bool has_f1 = false;
+  double* blk[9] = {};  // g1a g1b l2aa l2ab l2bb l3aaa l3aab l3abb l3bbb
+  // reference quantities on spin orbitals
+  Tensor gam, eta, L2, L3, F1;
+  // intermediates of the last evaluation
+  Tensor T1, T2, T1b, T2b, O1, O2;
+  long long launches = 0;
+  explicit Handle(cudaStream_t st) : stream(st), ws(st) {}
+};
+
+Tensor vclass(Handle& h, const Iv* ivs, double coef);
+void build_x(Handle& h, double c_v, const Tensor* W1, const Tensor* W2, double c_w, unsigned classes, Tensor& X1,
+             Sym2& X2);
+Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M);
+void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tensor& T2, Tensor& W1, Tensor& W2);
+void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef);
+void commutator(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
+                Tensor& C2, bool df, const Tensor* Wpp, double c_wpp);
+void commutator_A(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
+                  Tensor& O2, bool df, const Tensor* Wpp, double c_wpp);
+void scalar(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2);
+void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b);
+
+}  // namespace dsrg

@@ -1,0 +1,421 @@
+// Host-side tensor machinery (see engine.cuh).
+#include "engine.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <stdexcept>
+
+namespace dsrg {
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+View View::sub(const Iv* want) const {
+  View o = *this;
+  for (int k = 0; k < rank; ++k) {
+    if (!iv[k].contains(want[k])) throw std::runtime_error("view: requested interval outside the tensor");
+    o.p += (long long)(want[k].lo - iv[k].lo) * st[k];
+    o.iv[k] = want[k];
+  }
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+Workspace::~Workspace() {
+  for (auto& b : free_) cudaFree(b.p);
+  if (results) cudaFree(results);
+  if (dot_scratch) cudaFree(dot_scratch);
+}
+
+double* Workspace::get(size_t n, size_t& cap) {
+  if (n == 0) n = 1;
+  size_t best = (size_t)-1;
+  int bi = -1;
+  for (int i = 0; i < (int)free_.size(); ++i)
+    if (free_[i].n >= n && free_[i].n < best && free_[i].n <= 2 * n + (1 << 20)) {
+      best = free_[i].n;
+      bi = i;
+    }
+  double* p;
+  size_t got = n;
+  if (bi >= 0) {
+    p = free_[bi].p;
+    got = free_[bi].n;
+    free_.erase(free_.begin() + bi);
+  } else {
+    cudaError_t e = cudaMalloc(&p, n * sizeof(double));
+    if (e != cudaSuccess) {
+      // drop cached blocks and retry once
+      cudaGetLastError();
+      for (auto& b : free_) cudaFree(b.p);
+      free_.clear();
+      check_cuda(cudaMalloc(&p, n * sizeof(double)), "cudaMalloc");
+    }
+  }
+  in_use_ += got * sizeof(double);
+  peak_ = std::max(peak_, in_use_);
+  cap = got;
+  return p;
+}
+
+void Workspace::put(double* p, size_t cap) {
+  if (!p) return;
+  in_use_ -= cap * sizeof(double);
+  free_.push_back({p, cap});
+}
+
+Tensor& Tensor::operator=(Tensor&& o) noexcept {
+  if (this != &o) {
+    release();
+    v = o.v;
+    n = o.n;
+    cap = o.cap;
+    ws = o.ws;
+    o.v.p = nullptr;
+    o.n = 0;
+    o.cap = 0;
+    o.ws = nullptr;
+  }
+  return *this;
+}
+
+Tensor::~Tensor() { release(); }
+
+void Tensor::release() {
+  if (ws && v.p) ws->put(v.p, cap);
+  v.p = nullptr;
+  ws = nullptr;
+  n = 0;
+  cap = 0;
+}
+
+Tensor make_tensor(Workspace& ws, int rank, const Iv* ivs, bool zero) {
+  Tensor t;
+  t.v.rank = rank;
+  long long stride = 1;
+  for (int k = rank - 1; k >= 0; --k) {
+    t.v.iv[k] = ivs[k];
+    int L = ivs[k].len() > 0 ? ivs[k].len() : 0;
+    t.v.st[k] = stride;
+    t.v.ss[k] = (long long)L * stride;
+    stride *= 2LL * L;
+  }
+  t.n = (size_t)stride;
+  t.ws = &ws;
+  t.v.p = ws.get(t.n, t.cap);
+  if (zero) check_cuda(cudaMemsetAsync(t.v.p, 0, t.n * sizeof(double), ws.stream), "memset");
+  t.v.mask = 0;
+  return t;
+}
+
+uint64_t conserving_mask(int rank) {
+  int h = rank / 2;
+  uint64_t m = 0;
+  for (int b = 0; b < (1 << rank); ++b) {
+    int c = 0, a = 0;
+    for (int k = 0; k < h; ++k) c += (b >> k) & 1;
+    for (int k = h; k < rank; ++k) a += (b >> k) & 1;
+    if (c == a) m |= 1ULL << b;
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// label bookkeeping
+// ---------------------------------------------------------------------------
+namespace {
+struct Lab {
+  char c;
+  Iv iv;
+  int inA = -1, inB = -1, inC = -1;  // slot index in each operand
+};
+
+int find_lab(std::vector<Lab>& L, char c) {
+  for (int i = 0; i < (int)L.size(); ++i)
+    if (L[i].c == c) return i;
+  L.push_back(Lab{c, Iv{-1000000000, 1000000000}});
+  return (int)L.size() - 1;
+}
+
+void add_operand(std::vector<Lab>& L, const View& X, const char* lx, int which) {
+  int r = (int)strlen(lx);
+  if (r != X.rank) throw std::runtime_error(std::string("label count mismatch for ") + lx);
+  for (int k = 0; k < r; ++k) {
+    int i = find_lab(L, lx[k]);
+    L[i].iv = isect(L[i].iv, X.iv[k]);
+    if (which == 0) L[i].inA = k;
+    else if (which == 1) L[i].inB = k;
+    else L[i].inC = k;
+  }
+}
+
+View restrict_view(const View& X, const char* lx, const std::vector<Lab>& L) {
+  Iv want[kMaxRank];
+  for (int k = 0; k < X.rank; ++k) {
+    for (auto& l : L)
+      if (l.c == lx[k]) want[k] = l.iv;
+  }
+  return X.sub(want);
+}
+
+inline int spin_bits(const View& X, const char* lx, const std::vector<Lab>& L, int assign) {
+  int b = 0;
+  for (int k = 0; k < X.rank; ++k)
+    for (int i = 0; i < (int)L.size(); ++i)
+      if (L[i].c == lx[k]) b |= ((assign >> i) & 1) << k;
+  return b;
+}
+
+inline long long spin_off(const View& X, int bits) {
+  long long o = 0;
+  for (int k = 0; k < X.rank; ++k)
+    if ((bits >> k) & 1) o += X.ss[k];
+  return o;
+}
+
+struct Dim {
+  int e;
+  long long s1, s2;
+};
+
+void fill_group(std::vector<Dim>& d, int& n, int* e, long long* s1, long long* s2) {
+  if (d.size() > 4) throw std::runtime_error("contraction group with more than four dimensions");
+  // slowest first; fastest (smallest first stride) last
+  std::sort(d.begin(), d.end(), [](const Dim& a, const Dim& b) { return a.s1 > b.s1; });
+  n = (int)d.size();
+  for (int i = 0; i < n; ++i) {
+    e[i] = d[i].e;
+    s1[i] = d[i].s1;
+    s2[i] = d[i].s2;
+  }
+}
+}  // namespace
+
+bool contract(Workspace& ws, double alpha, const View& A, const char* la, const View& B, const char* lb, Tensor& C,
+              const char* lc) {
+  std::vector<Lab> L;
+  add_operand(L, A, la, 0);
+  add_operand(L, B, lb, 1);
+  add_operand(L, C.v, lc, 2);
+  for (auto& l : L)
+    if (l.iv.empty()) return false;
+  if (L.size() > 16) throw std::runtime_error("too many labels");
+  View a = restrict_view(A, la, L), b = restrict_view(B, lb, L), c = restrict_view(C.v, lc, L);
+  bool any = false;
+  for (int assign = 0; assign < (1 << L.size()); ++assign) {
+    int ba = spin_bits(a, la, L, assign), bb = spin_bits(b, lb, L, assign), bc = spin_bits(c, lc, L, assign);
+    if (!((a.mask >> ba) & 1) || !((b.mask >> bb) & 1)) continue;
+    GemmArgs g{};
+    g.A = a.p + spin_off(a, ba);
+    g.B = b.p + spin_off(b, bb);
+    g.C = c.p + spin_off(c, bc);
+    g.alpha = alpha;
+    std::vector<Dim> M, N, K, Bt;
+    for (auto& l : L) {
+      int e = l.iv.len();
+      bool iA = l.inA >= 0, iB = l.inB >= 0, iC = l.inC >= 0;
+      if (iA && iB && iC) Bt.push_back({e, a.st[l.inA], b.st[l.inB]});
+      else if (iA && iC) M.push_back({e, a.st[l.inA], c.st[l.inC]});
+      else if (iB && iC) N.push_back({e, b.st[l.inB], c.st[l.inC]});
+      else if (iA && iB) K.push_back({e, a.st[l.inA], b.st[l.inB]});
+      else throw std::runtime_error(std::string("label only in one operand: ") + l.c);
+    }
+    fill_group(M, g.nM, g.eM, g.aM, g.cM);
+    fill_group(N, g.nN, g.eN, g.bN, g.cN);
+    fill_group(K, g.nK, g.eK, g.aK, g.bK);
+    // batch labels need a C stride too
+    {
+      std::sort(Bt.begin(), Bt.end(), [](const Dim& x, const Dim& y) { return x.s1 > y.s1; });
+      if (Bt.size() > 4) throw std::runtime_error("too many batch labels");
+      g.nB = (int)Bt.size();
+      for (int i = 0; i < g.nB; ++i) {
+        g.eB[i] = Bt[i].e;
+        g.aB[i] = Bt[i].s1;
+        g.bB[i] = Bt[i].s2;
+      }
+      // C strides of batch labels, in the same order
+      int bi = 0;
+      std::vector<std::pair<long long, long long>> cb;
+      for (auto& l : L)
+        if (l.inA >= 0 && l.inB >= 0 && l.inC >= 0) cb.push_back({a.st[l.inA], c.st[l.inC]});
+      std::sort(cb.begin(), cb.end(), [](auto& x, auto& y) { return x.first > y.first; });
+      for (auto& x : cb) g.cB[bi++] = x.second;
+    }
+    g.M = g.N = g.K = g.nbatch = 1;
+    for (int i = 0; i < g.nM; ++i) g.M *= g.eM[i];
+    for (int i = 0; i < g.nN; ++i) g.N *= g.eN[i];
+    for (int i = 0; i < g.nK; ++i) g.K *= g.eK[i];
+    for (int i = 0; i < g.nB; ++i) g.nbatch *= g.eB[i];
+    if (g.nbatch > 65535) throw std::runtime_error("batch too large");
+    launch_gemm(g, ws.stream);
+    ws.launches++;
+    C.v.mask |= 1ULL << bc;
+    any = true;
+  }
+  return any;
+}
+
+void axpy(Workspace& ws, double alpha, const View& A, const char* la, Tensor& C, const char* lc) {
+  std::vector<Lab> L;
+  add_operand(L, A, la, 0);
+  add_operand(L, C.v, lc, 2);
+  for (auto& l : L) {
+    if (l.iv.empty()) return;
+    if (l.inA < 0 || l.inC < 0) throw std::runtime_error("axpy: label sets differ");
+  }
+  View a = restrict_view(A, la, L), c = restrict_view(C.v, lc, L);
+  for (int assign = 0; assign < (1 << L.size()); ++assign) {
+    int ba = spin_bits(a, la, L, assign), bc = spin_bits(c, lc, L, assign);
+    if (!((a.mask >> ba) & 1)) continue;
+    NdArgs g{};
+    g.nd = (int)L.size();
+    g.total = 1;
+    for (int i = 0; i < g.nd; ++i) {
+      g.e[i] = L[i].iv.len();
+      g.sa[i] = a.st[L[i].inA];
+      g.sb[i] = c.st[L[i].inC];
+      g.total *= g.e[i];
+    }
+    launch_axpy(g, alpha, a.p + spin_off(a, ba), c.p + spin_off(c, bc), ws.stream);
+    ws.launches++;
+    C.v.mask |= 1ULL << bc;
+  }
+}
+
+void dot(Workspace& ws, double alpha, const View& A, const char* la, const View& B, const char* lb) {
+  std::vector<Lab> L;
+  add_operand(L, A, la, 0);
+  add_operand(L, B, lb, 1);
+  for (auto& l : L) {
+    if (l.iv.empty()) return;
+    if (l.inA < 0 || l.inB < 0) throw std::runtime_error("dot: label sets differ");
+  }
+  View a = restrict_view(A, la, L), b = restrict_view(B, lb, L);
+  for (int assign = 0; assign < (1 << L.size()); ++assign) {
+    int ba = spin_bits(a, la, L, assign), bb = spin_bits(b, lb, L, assign);
+    if (!((a.mask >> ba) & 1) || !((b.mask >> bb) & 1)) continue;
+    NdArgs g{};
+    g.nd = (int)L.size();
+    g.total = 1;
+    for (int i = 0; i < g.nd; ++i) {
+      g.e[i] = L[i].iv.len();
+      g.sa[i] = a.st[L[i].inA];
+      g.sb[i] = b.st[L[i].inB];
+      g.total *= g.e[i];
+    }
+    if (ws.nresults >= ws.cap_results) throw std::runtime_error("out of result slots");
+    int r = ws.nresults++;
+    launch_dot(g, alpha, a.p + spin_off(a, ba), b.p + spin_off(b, bb), ws.dot_scratch, ws.dot_scratch_len,
+               ws.results + r, ws.stream);
+    ws.launches += 2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// symmetric two-body store
+// ---------------------------------------------------------------------------
+namespace {
+// X[w0,w1,w2,w3] = sign * T[w_perm0, w_perm1, w_perm2, w_perm3]
+const int kOps[8][4] = {{0, 1, 2, 3}, {1, 0, 2, 3}, {0, 1, 3, 2}, {1, 0, 3, 2},
+                        {2, 3, 0, 1}, {3, 2, 0, 1}, {2, 3, 1, 0}, {3, 2, 1, 0}};
+const double kSign[8] = {1, -1, -1, 1, 1, -1, -1, 1};
+}  // namespace
+
+bool Sym2::resolve(const Iv* want, View& out, double& sign) const {
+  for (auto& t : cls) {
+    for (int o = 0; o < 8; ++o) {
+      const int* pm = kOps[o];
+      bool ok = true;
+      for (int k = 0; k < 4 && ok; ++k) ok = t.v.iv[k].contains(want[pm[k]]);
+      if (!ok) continue;
+      // request slot j is class slot k with pm[k] == j
+      View v;
+      v.rank = 4;
+      v.p = t.v.p;
+      for (int k = 0; k < 4; ++k) {
+        int j = pm[k];
+        v.p += (long long)(want[j].lo - t.v.iv[k].lo) * t.v.st[k];
+        v.iv[j] = want[j];
+        v.st[j] = t.v.st[k];
+        v.ss[j] = t.v.ss[k];
+      }
+      v.mask = 0;
+      for (int b = 0; b < 16; ++b) {
+        if (!((t.v.mask >> b) & 1)) continue;
+        int vb = 0;
+        for (int k = 0; k < 4; ++k) vb |= ((b >> k) & 1) << pm[k];
+        v.mask |= 1ULL << vb;
+      }
+      out = v;
+      sign = kSign[o];
+      return true;
+    }
+  }
+  return false;
+}
+
+static void x2_request(const char* lx, const std::vector<Lab>& L, Iv* want) {
+  for (int k = 0; k < 4; ++k) {
+    want[k] = Iv{-1000000000, 1000000000};
+    for (auto& l : L)
+      if (l.c == lx[k]) want[k] = l.iv;
+  }
+}
+
+bool contract_x2(Workspace& ws, double alpha, const Sym2& X, const char* lx, const View& B, const char* lb, Tensor& C,
+                 const char* lc, const Iv* extra_ivs, const char* extra_labs) {
+  std::vector<Lab> L;
+  add_operand(L, B, lb, 1);
+  add_operand(L, C.v, lc, 2);
+  if (extra_labs)
+    for (int i = 0; extra_labs[i]; ++i) {
+      int j = find_lab(L, extra_labs[i]);
+      L[j].iv = isect(L[j].iv, extra_ivs[i]);
+    }
+  for (auto& l : L)
+    if (l.iv.empty()) return false;
+  Iv want[4];
+  x2_request(lx, L, want);
+  for (int k = 0; k < 4; ++k)
+    if (want[k].lo < -100000000) throw std::runtime_error(std::string("unconstrained two-body label in ") + lx);
+  View xv;
+  double sg;
+  if (!X.resolve(want, xv, sg)) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "no stored two-body class covers [%d,%d)x[%d,%d)x[%d,%d)x[%d,%d) for %s", want[0].lo,
+             want[0].hi, want[1].lo, want[1].hi, want[2].lo, want[2].hi, want[3].lo, want[3].hi, lx);
+    throw std::runtime_error(buf);
+  }
+  return contract(ws, alpha * sg, xv, lx, B, lb, C, lc);
+}
+
+bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la, const Sym2& X, const char* lx,
+                      Tensor& C, const char* lc) {
+  std::vector<Lab> L;
+  add_operand(L, A, la, 0);
+  add_operand(L, C.v, lc, 2);
+  for (auto& l : L)
+    if (l.iv.empty()) return false;
+  Iv want[4];
+  x2_request(lx, L, want);
+  for (int k = 0; k < 4; ++k)
+    if (want[k].lo < -100000000) throw std::runtime_error(std::string("unconstrained two-body label in ") + lx);
+  View xv;
+  double sg;
+  if (!X.resolve(want, xv, sg)) throw std::runtime_error(std::string("no stored two-body class for ") + lx);
+  return contract(ws, alpha * sg, A, la, xv, lx, C, lc);
+}
+
+void dot_x2(Workspace& ws, double alpha, const Sym2& X, const Tensor& U) {
+  for (int k = 0; k < 4; ++k)
+    if (U.v.iv[k].empty()) return;
+  View xv;
+  double sg;
+  if (!X.resolve(U.v.iv, xv, sg)) throw std::runtime_error("no stored two-body class for a scalar term");
+  dot(ws, alpha * sg, xv, "pqrs", U.v, "pqrs");
+}
+
+}  // namespace dsrg

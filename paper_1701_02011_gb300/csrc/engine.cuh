@@ -1,0 +1,111 @@
+// Host-side tensor machinery for the DSRG-MRPT2/PT3 energy path.
+//
+// A spin-orbital tensor slot covers an interval [lo, hi) of spatial orbitals
+// (global numbering: core [0,c), active [c,c+a), virtual [c+a,n)) for both
+// spins, laid out spin-major.  Contractions intersect the intervals of every
+// label across operands, so a term written once over hole (H = core+active)
+// and particle (P = active+virtual) ranges automatically restricts to the
+// overlap (the active space) where two different ranges meet.  Spin blocks
+// that are identically zero are tracked by a bit mask and skipped.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace dsrg {
+
+struct Iv {
+  int lo = 0, hi = 0;
+  int len() const { return hi - lo; }
+  bool empty() const { return hi <= lo; }
+  bool contains(const Iv& o) const { return lo <= o.lo && o.hi <= hi; }
+};
+inline Iv isect(Iv a, Iv b) { return Iv{a.lo > b.lo ? a.lo : b.lo, a.hi < b.hi ? a.hi : b.hi}; }
+
+constexpr int kMaxRank = 6;
+
+struct View {
+  double* p = nullptr;  // element with every slot at (spin 0, iv.lo)
+  int rank = 0;
+  Iv iv[kMaxRank];
+  long long st[kMaxRank] = {0};  // stride of the spatial index
+  long long ss[kMaxRank] = {0};  // stride of the spin index
+  uint64_t mask = 0;              // bit b set: spin block with spins (bit k of b) may be non-zero
+  View sub(const Iv* want) const;
+};
+
+class Workspace;
+
+struct Tensor {
+  View v;
+  size_t n = 0;    // elements
+  size_t cap = 0;  // elements of the underlying block
+  Workspace* ws = nullptr;
+  Tensor() = default;
+  Tensor(const Tensor&) = delete;
+  Tensor& operator=(const Tensor&) = delete;
+  Tensor(Tensor&& o) noexcept { *this = std::move(o); }
+  Tensor& operator=(Tensor&& o) noexcept;
+  ~Tensor();
+  void release();
+};
+
+// Device memory for tensors: blocks are cached by size and reused, so after
+// the first energy evaluation no further cudaMalloc happens.
+class Workspace {
+ public:
+  explicit Workspace(cudaStream_t st) : stream(st) {}
+  ~Workspace();
+  double* get(size_t n, size_t& cap);
+  void put(double* p, size_t cap);
+  size_t bytes_in_use() const { return in_use_; }
+  size_t peak_bytes() const { return peak_; }
+  cudaStream_t stream;
+  // result slots of scalar reductions (device) and their host copy
+  double* results = nullptr;
+  int nresults = 0, cap_results = 0;
+  double* dot_scratch = nullptr;
+  int dot_scratch_len = 0;
+  int launches = 0;
+
+ private:
+  struct Blk { double* p; size_t n; };
+  std::vector<Blk> free_;
+  size_t in_use_ = 0, peak_ = 0;
+};
+
+Tensor make_tensor(Workspace& ws, int rank, const Iv* ivs, bool zero = true);
+// Mask of a tensor whose first rank/2 slots are creators and the rest
+// annihilators: non-zero only when the alpha counts agree.
+uint64_t conserving_mask(int rank);
+
+// C[lc] += alpha * A[la] * B[lb] (labels are characters; labels shared by A and
+// B but absent from C are summed).  Returns false if nothing was launched.
+bool contract(Workspace& ws, double alpha, const View& A, const char* la, const View& B, const char* lb,
+              Tensor& C, const char* lc);
+// C[lc] += alpha * A[la] with the same label set.
+void axpy(Workspace& ws, double alpha, const View& A, const char* la, Tensor& C, const char* lc);
+// alpha * sum over all labels of A[la] * B[lb] (identical label sets); each
+// spin block's value lands in the next free device result slot.
+void dot(Workspace& ws, double alpha, const View& A, const char* la, const View& B, const char* lb);
+
+// Two-body operator with the symmetries of an antisymmetrised Hermitian
+// operator, stored on a few canonical interval classes; a request for any
+// other class is served as a permuted view with a sign.
+struct Sym2 {
+  std::vector<Tensor> cls;
+  bool resolve(const Iv* want, View& out, double& sign) const;
+};
+
+// C[lc] += alpha * X2[lx] * B[lb] with X2 served from the store.
+bool contract_x2(Workspace& ws, double alpha, const Sym2& X, const char* lx, const View& B, const char* lb,
+                 Tensor& C, const char* lc, const Iv* extra_lab_ivs = nullptr, const char* extra_labs = nullptr);
+bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la, const Sym2& X, const char* lx,
+                      Tensor& C, const char* lc);
+void dot_x2(Workspace& ws, double alpha, const Sym2& X, const Tensor& U);
+
+void check_cuda(cudaError_t e, const char* what);
+
+}  // namespace dsrg
