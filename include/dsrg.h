@@ -114,6 +114,23 @@ const char *dsrg_last_error(void);
  * dsrg_pt3 call on the handle (-1 on a NULL handle). */
 long long dsrg_last_launch_count(const dsrg_handle *h);
 
+/* Per-kernel timing.  dsrg_profile(h, 1) makes later dsrg_pt2/dsrg_pt3 calls
+ * bracket every launch of this library with CUDA events on the handle's
+ * stream and accumulate, per kernel, the launch count, the summed device
+ * time (ms), the executed FP64 flops (2 M N K per contraction) and the bytes
+ * moved by elementwise kernels; dsrg_profile(h, 0) stops.  Both reset the
+ * totals.  dsrg_profile_stats reads kernel index 0 .. 5 (generic
+ * contraction, ladder (pr|qs) build, ladder contraction, axpy, dot,
+ * amplitude kernels); *name receives a static string.  DSRG_ERR_ARG past the
+ * last index. */
+int dsrg_profile(dsrg_handle *h, int enable);
+int dsrg_profile_stats(const dsrg_handle *h, int kernel, const char **name, long long *launches, double *ms,
+                       double *flops, double *bytes);
+
+/* Device-to-host bytes read back by the last dsrg_pt2 / dsrg_pt3 call (the
+ * per-block partial sums of the energy components; -1 on a NULL handle). */
+long long dsrg_last_d2h_bytes(const dsrg_handle *h);
+
 /* Peak device bytes held by the handle's tensor workspace. */
 long long dsrg_peak_bytes(const dsrg_handle *h);
 

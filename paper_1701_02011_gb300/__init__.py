@@ -43,7 +43,8 @@ class dsrg_energies(ctypes.Structure):
 
 
 EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_free", "dsrg_last_error",
-           "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch")
+           "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
+           "dsrg_last_d2h_bytes")
 
 _lib = None
 
@@ -69,10 +70,17 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
     L.dsrg_last_error.restype = ctypes.c_char_p
     L.dsrg_last_launch_count.argtypes = [ctypes.c_void_p]
     L.dsrg_last_launch_count.restype = ctypes.c_longlong
+    L.dsrg_last_d2h_bytes.argtypes = [ctypes.c_void_p]
+    L.dsrg_last_d2h_bytes.restype = ctypes.c_longlong
     L.dsrg_peak_bytes.argtypes = [ctypes.c_void_p]
     L.dsrg_peak_bytes.restype = ctypes.c_longlong
     L.dsrg_fetch.argtypes = [ctypes.c_void_p, ctypes.c_char_p, _P, ctypes.c_longlong]
     L.dsrg_fetch.restype = ctypes.c_int
+    L.dsrg_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    L.dsrg_profile.restype = ctypes.c_int
+    L.dsrg_profile_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                     ctypes.POINTER(ctypes.c_longlong), _P, _P, _P]
+    L.dsrg_profile_stats.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -163,8 +171,34 @@ def dsrg_last_launch_count(h) -> int:
     return int(load_library().dsrg_last_launch_count(h))
 
 
+def dsrg_last_d2h_bytes(h) -> int:
+    return int(load_library().dsrg_last_d2h_bytes(h))
+
+
 def dsrg_peak_bytes(h) -> int:
     return int(load_library().dsrg_peak_bytes(h))
+
+
+def dsrg_profile(h, enable: bool) -> None:
+    _check(load_library().dsrg_profile(h, 1 if enable else 0))
+
+
+def dsrg_profile_stats(h) -> dict:
+    """{kernel name: dict(launches, ms, flops, bytes)} accumulated since dsrg_profile."""
+    L = load_library()
+    out = {}
+    k = 0
+    while True:
+        name = ctypes.c_char_p()
+        n = ctypes.c_longlong()
+        ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        rc = L.dsrg_profile_stats(h, k, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                  ctypes.byref(by))
+        if rc != 0:
+            break
+        out[name.value.decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+        k += 1
+    return out
 
 
 def tensor_shape(name: str, nc: int, na: int, nv: int):
@@ -201,6 +235,12 @@ class Dsrg:
 
     def fetch(self, name):
         return dsrg_fetch(self.h, name, *self.sizes)
+
+    def profile(self, enable=True):
+        dsrg_profile(self.h, enable)
+
+    def profile_stats(self):
+        return dsrg_profile_stats(self.h)
 
     @property
     def launches(self):

@@ -89,10 +89,7 @@ void load_inputs(dsrg::Handle& h, const dsrg_inputs* in) {
   }
   h.has_f1 = in->f1 != nullptr;
   if (h.has_f1) {
-    if (!h.f1raw) {
-      size_t cap;
-      h.f1raw = h.ws.get((size_t)n * n, cap);
-    }
+    if (!h.f1raw) h.f1raw = h.own((size_t)n * n);
     copy_in(h.f1raw, in->f1, (size_t)n * n, in->memory, st);
     // spin-orbital [G,G]: f1 on both spin diagonal blocks, its core-core,
     // active-active and virtual-virtual parts removed (those are in H(0))
@@ -160,12 +157,11 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
     h->H = {0, in->nc + in->na};
     h->P = {in->nc, h->n};
     h->G = {0, h->n};
-    size_t cap;
-    h->eps = h->ws.get((size_t)h->n, cap);
-    h->B = h->ws.get((size_t)h->naux * h->n * h->n, cap);
+    h->eps = h->own((size_t)h->n);
+    h->B = h->own((size_t)h->naux * h->n * h->n);
     const int rank[9] = {2, 2, 4, 4, 4, 6, 6, 6, 6};
     if (h->na > 0)
-      for (int k = 0; k < 9; ++k) h->blk[k] = h->ws.get(pow_na(h->na, rank[k]), cap);
+      for (int k = 0; k < 9; ++k) h->blk[k] = h->own(pow_na(h->na, rank[k]));
     h->ws.cap_results = 1 << 16;
     dsrg::check_cuda(cudaMalloc(&h->ws.results, h->ws.cap_results * sizeof(double)), "cudaMalloc (results)");
     h->ws.dot_scratch_len = 2 * 152 * 16;
@@ -215,6 +211,7 @@ static int run(dsrg_handle* hd, bool pt3, dsrg_energies* out) {
     dsrg::run_energy(*hd->h, pt3, &e2, &e3a, &e3b);
     dsrg::check_cuda(cudaGetLastError(), "kernel launch");
     dsrg::check_cuda(cudaStreamSynchronize(hd->h->stream), "cudaStreamSynchronize");
+    hd->h->ws.prof_collect();
     out->e2 = e2;
     out->e3a = e3a;
     out->e3b = e3b;
@@ -243,6 +240,32 @@ void dsrg_free(dsrg_handle* hd) {
 long long dsrg_last_launch_count(const dsrg_handle* hd) {
   if (!hd || !hd->h) return -1;
   return hd->h->launches;
+}
+
+int dsrg_profile(dsrg_handle* hd, int enable) {
+  g_last_error.clear();
+  if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
+  hd->h->ws.profiling = enable != 0;
+  hd->h->ws.prof_reset();
+  return DSRG_OK;
+}
+
+int dsrg_profile_stats(const dsrg_handle* hd, int kernel, const char** name, long long* launches, double* ms,
+                       double* flops, double* bytes) {
+  if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
+  if (kernel < 0 || kernel >= dsrg::K_NKERNELS) return fail(DSRG_ERR_ARG, "kernel index out of range");
+  const dsrg::Workspace& w = hd->h->ws;
+  if (name) *name = dsrg::kernel_name(kernel);
+  if (launches) *launches = w.prof_launches[kernel];
+  if (ms) *ms = w.prof_ms[kernel];
+  if (flops) *flops = w.prof_flops[kernel];
+  if (bytes) *bytes = w.prof_bytes[kernel];
+  return DSRG_OK;
+}
+
+long long dsrg_last_d2h_bytes(const dsrg_handle* hd) {
+  if (!hd || !hd->h) return -1;
+  return hd->h->d2h_bytes;
 }
 
 long long dsrg_peak_bytes(const dsrg_handle* hd) {

@@ -32,8 +32,7 @@ void raw_axpy4(Handle& h, double alpha, const double* src, const long long* ss, 
     g.sb[i] = ds[i];
     g.total *= ext[i];
   }
-  launch_axpy(g, alpha, src, dst, h.ws.stream);
-  h.ws.launches++;
+  run_axpy(h.ws, g, alpha, src, dst);
 }
 
 // J[p,q,r,s] = sum_Q B[Q,p,r] B[Q,q,s] for p in I0, q in I1, r in I2, s in I3,
@@ -59,8 +58,7 @@ void df_integrals(Handle& h, Iv I0, Iv I1, Iv I2, Iv I3, double* J) {
   g.N = (long long)L1 * L3;
   g.K = h.naux;
   g.nbatch = 1;
-  launch_gemm(g, h.ws.stream);
-  h.ws.launches++;
+  run_gemm(h.ws, g);
 }
 }  // namespace
 
@@ -144,8 +142,9 @@ static Tensor gamma_source(Handle& h, const Tensor& T2) {
   Tensor S = mk(h, {h.P, h.H});
   if (h.na > 0) {
     Tensor G = mk(h, {h.A, h.A}, false);
+    int r = h.ws.begin(K_AMP, 0.0, 0.0);
     launch_gamma_delta(h.nc, h.na, h.eps, h.gam.v.p, h.nc + h.na, G.v.p, h.ws.stream);
-    h.ws.launches++;
+    h.ws.end(r);
     G.v.mask = conserving_mask(2);
     contract(h.ws, 1.0, T2.v, "axiu", G.v, "xu", S, "ai");
   }
@@ -156,14 +155,20 @@ static Tensor gamma_source(Handle& h, const Tensor& T2) {
 void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tensor& T2, Tensor& W1, Tensor& W2) {
   T2 = mk(h, {h.P, h.P, h.H, h.H}, false);
   W2 = mk(h, {h.P, h.P, h.H, h.H}, false);
-  launch_amp2(h.nc, h.na, h.nv, h.s, h.eps, O2.v.p, T2.v.p, W2.v.p, h.ws.stream);
-  h.ws.launches++;
+  {
+    int r = h.ws.begin(K_AMP, 0.0, 24.0 * (double)T2.n);
+    launch_amp2(h.nc, h.na, h.nv, h.s, h.eps, O2.v.p, T2.v.p, W2.v.p, h.ws.stream);
+    h.ws.end(r);
+  }
   T2.v.mask = W2.v.mask = conserving_mask(4);
   Tensor S = gamma_source(h, T2);
   T1 = mk(h, {h.P, h.H}, false);
   W1 = mk(h, {h.P, h.H}, false);
-  launch_amp1(h.nc, h.na, h.nv, h.s, h.eps, O1 ? O1->v.p : nullptr, S.v.p, T1.v.p, W1.v.p, h.ws.stream);
-  h.ws.launches++;
+  {
+    int r = h.ws.begin(K_AMP, 0.0, 40.0 * (double)T1.n);
+    launch_amp1(h.nc, h.na, h.nv, h.s, h.eps, O1 ? O1->v.p : nullptr, S.v.p, T1.v.p, W1.v.p, h.ws.stream);
+    h.ws.end(r);
+  }
   T1.v.mask = W1.v.mask = conserving_mask(2);
 }
 
@@ -210,8 +215,7 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
       g.N = (long long)p * p;
       g.K = h.naux;
       g.nbatch = 1;
-      launch_gemm(g, h.ws.stream);
-      h.ws.launches++;
+      run_gemm(h.ws, g, K_LADDER_BUILD);
     }
     {  // L[p0+pp,q,i,j] += sum_{r,s} G[pp,q,r,s] t[r,s,i,j]
       GemmArgs g{};
@@ -232,8 +236,7 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
       g.N = (long long)hh * hh;
       g.K = (long long)p * p;
       g.nbatch = 1;
-      launch_gemm(g, h.ws.stream);
-      h.ws.launches++;
+      run_gemm(h.ws, g, K_LADDER_CONTRACT);
     }
   }
   h.ws.put(G, capG);
@@ -511,6 +514,7 @@ void scalar(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const
 static double sum_results(Handle& h, int lo, int hi) {
   if (hi <= lo) return 0.0;
   std::vector<double> v(hi - lo);
+  h.d2h_bytes += (long long)(hi - lo) * (long long)sizeof(double);
   check_cuda(cudaMemcpyAsync(v.data(), h.ws.results + lo, (hi - lo) * sizeof(double), cudaMemcpyDeviceToHost,
                              h.ws.stream),
              "copy results");
@@ -527,6 +531,7 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   Workspace& ws = h.ws;
   ws.launches = 0;
   ws.nresults = 0;
+  h.d2h_bytes = 0;
   const Iv& H = h.H;
   const Iv& P = h.P;
   // first-order amplitudes from the non-diagonal part of H(1)

@@ -22,7 +22,19 @@ struct Handle {
   // intermediates of the last evaluation
   Tensor T1, T2, T1b, T2b, O1, O2;
   long long launches = 0;
+  long long d2h_bytes = 0;
+  // raw device buffers taken from the workspace (returned on destruction)
+  std::vector<std::pair<double*, size_t>> owned;
+  double* own(size_t n) {
+    size_t cap;
+    double* p = ws.get(n, cap);
+    owned.push_back({p, cap});
+    return p;
+  }
   explicit Handle(cudaStream_t st) : stream(st), ws(st) {}
+  ~Handle() {
+    for (auto& b : owned) ws.put(b.first, b.second);
+  }
 };
 
 Tensor vclass(Handle& h, const Iv* ivs, double coef);

@@ -21,10 +21,84 @@ View View::sub(const Iv* want) const {
   return o;
 }
 
+const char* kernel_name(int id) {
+  switch (id) {
+    case K_GEMM: return "k_gemm<0>";
+    case K_LADDER_BUILD: return "k_gemm<1>";
+    case K_LADDER_CONTRACT: return "k_gemm<2>";
+    case K_AXPY: return "k_axpy";
+    case K_DOT: return "k_dot";
+    case K_AMP: return "k_amp";
+    default: return "?";
+  }
+}
+
 // ---------------------------------------------------------------------------
 // workspace
 // ---------------------------------------------------------------------------
+void Workspace::prof_reset() {
+  for (int i = 0; i < K_NKERNELS; ++i) {
+    prof_launches[i] = 0;
+    prof_ms[i] = prof_flops[i] = prof_bytes[i] = 0.0;
+  }
+}
+
+int Workspace::begin(int id, double flops, double bytes) {
+  launches++;
+  if (!profiling) return -1;
+  Rec r{id, nullptr, nullptr, flops, bytes};
+  for (cudaEvent_t* e : {&r.a, &r.b}) {
+    if (!ev_pool.empty()) {
+      *e = ev_pool.back();
+      ev_pool.pop_back();
+    } else {
+      check_cuda(cudaEventCreate(e), "cudaEventCreate");
+    }
+  }
+  check_cuda(cudaEventRecord(r.a, stream), "cudaEventRecord");
+  recs.push_back(r);
+  return (int)recs.size() - 1;
+}
+
+void Workspace::end(int rec) {
+  if (rec < 0) return;
+  check_cuda(cudaEventRecord(recs[rec].b, stream), "cudaEventRecord");
+}
+
+void Workspace::prof_collect() {
+  for (auto& r : recs) {
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+    prof_launches[r.id]++;
+    prof_ms[r.id] += ms;
+    prof_flops[r.id] += r.flops;
+    prof_bytes[r.id] += r.bytes;
+    ev_pool.push_back(r.a);
+    ev_pool.push_back(r.b);
+  }
+  recs.clear();
+}
+
+void run_gemm(Workspace& ws, const GemmArgs& g, int kind) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nbatch <= 0) return;
+  int r = ws.begin(kind, 2.0 * (double)g.M * (double)g.N * (double)g.K * (double)g.nbatch, 0.0);
+  launch_gemm(g, ws.stream, kind == K_LADDER_BUILD ? 1 : kind == K_LADDER_CONTRACT ? 2 : 0);
+  ws.end(r);
+}
+
+void run_axpy(Workspace& ws, const NdArgs& g, double alpha, const double* A, double* C) {
+  if (g.total <= 0) return;
+  int r = ws.begin(K_AXPY, 0.0, 24.0 * (double)g.total);
+  launch_axpy(g, alpha, A, C, ws.stream);
+  ws.end(r);
+}
+
 Workspace::~Workspace() {
+  for (auto& r : recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ev_pool) cudaEventDestroy(e);
   for (auto& b : free_) cudaFree(b.p);
   if (results) cudaFree(results);
   if (dot_scratch) cudaFree(dot_scratch);
@@ -250,8 +324,7 @@ bool contract(Workspace& ws, double alpha, const View& A, const char* la, const 
     for (int i = 0; i < g.nK; ++i) g.K *= g.eK[i];
     for (int i = 0; i < g.nB; ++i) g.nbatch *= g.eB[i];
     if (g.nbatch > 65535) throw std::runtime_error("batch too large");
-    launch_gemm(g, ws.stream);
-    ws.launches++;
+    run_gemm(ws, g);
     C.v.mask |= 1ULL << bc;
     any = true;
   }
@@ -279,8 +352,7 @@ void axpy(Workspace& ws, double alpha, const View& A, const char* la, Tensor& C,
       g.sb[i] = c.st[L[i].inC];
       g.total *= g.e[i];
     }
-    launch_axpy(g, alpha, a.p + spin_off(a, ba), c.p + spin_off(c, bc), ws.stream);
-    ws.launches++;
+    run_axpy(ws, g, alpha, a.p + spin_off(a, ba), c.p + spin_off(c, bc));
     C.v.mask |= 1ULL << bc;
   }
 }
@@ -308,9 +380,11 @@ void dot(Workspace& ws, double alpha, const View& A, const char* la, const View&
     }
     if (ws.nresults >= ws.cap_results) throw std::runtime_error("out of result slots");
     int r = ws.nresults++;
+    int rec = ws.begin(K_DOT, 2.0 * (double)g.total, 16.0 * (double)g.total);
+    ws.launches++;  // partial + final reduction
     launch_dot(g, alpha, a.p + spin_off(a, ba), b.p + spin_off(b, bb), ws.dot_scratch, ws.dot_scratch_len,
                ws.results + r, ws.stream);
-    ws.launches += 2;
+    ws.end(rec);
   }
 }
 

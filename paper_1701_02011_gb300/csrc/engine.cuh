@@ -38,6 +38,11 @@ struct View {
 
 class Workspace;
 
+// Kernels whose launches can be timed one by one (opt-in) with CUDA events on
+// the launching stream.
+enum KernelId { K_GEMM = 0, K_LADDER_BUILD, K_LADDER_CONTRACT, K_AXPY, K_DOT, K_AMP, K_NKERNELS };
+const char* kernel_name(int id);
+
 struct Tensor {
   View v;
   size_t n = 0;    // elements
@@ -68,7 +73,19 @@ class Workspace {
   int nresults = 0, cap_results = 0;
   double* dot_scratch = nullptr;
   int dot_scratch_len = 0;
-  int launches = 0;
+  long long launches = 0;
+  // opt-in per-launch timing
+  bool profiling = false;
+  struct Rec { int id; cudaEvent_t a, b; double flops, bytes; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> ev_pool;
+  long long prof_launches[K_NKERNELS] = {0};
+  double prof_ms[K_NKERNELS] = {0}, prof_flops[K_NKERNELS] = {0}, prof_bytes[K_NKERNELS] = {0};
+  void prof_reset();
+  // brackets one launch; call begin() before and end() after it
+  int begin(int id, double flops, double bytes);
+  void end(int rec);
+  void prof_collect();  // after the stream is synchronised
 
  private:
   struct Blk { double* p; size_t n; };
@@ -107,5 +124,9 @@ bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la
 void dot_x2(Workspace& ws, double alpha, const Sym2& X, const Tensor& U);
 
 void check_cuda(cudaError_t e, const char* what);
+
+// launches through the workspace (counted, optionally timed)
+void run_gemm(Workspace& ws, const GemmArgs& g, int kind = K_GEMM);
+void run_axpy(Workspace& ws, const NdArgs& g, double alpha, const double* A, double* C);
 
 }  // namespace dsrg

@@ -28,6 +28,7 @@ __device__ __forceinline__ void decode(long long lin, int nd, const int* ext, co
   }
 }
 
+template <int TAG>
 __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
   __shared__ double As[BK][BM];
   __shared__ double Bs[BK][BN];
@@ -348,10 +349,14 @@ inline int grid_for(long long n, int threads, int cap = 152 * 16) {
 }
 }  // namespace
 
-void launch_gemm(const GemmArgs& g, cudaStream_t st) {
+void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nbatch <= 0) return;
   dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)g.nbatch);
-  k_gemm<<<grid, NT, 0, st>>>(g);
+  switch (kind) {
+    case 1: k_gemm<1><<<grid, NT, 0, st>>>(g); break;   // (pr|qs) build from B
+    case 2: k_gemm<2><<<grid, NT, 0, st>>>(g); break;   // ladder contraction with T2
+    default: k_gemm<0><<<grid, NT, 0, st>>>(g); break;  // every other contraction
+  }
 }
 
 void launch_axpy(const NdArgs& g, double alpha, const double* A, double* C, cudaStream_t st) {

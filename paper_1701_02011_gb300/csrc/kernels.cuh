@@ -41,7 +41,8 @@ void launch_axpy(const NdArgs& g, double alpha, const double* A, double* C, cuda
 // partial[slot] = alpha * sum A[idx] * B[idx]; deterministic two-pass reduction.
 void launch_dot(const NdArgs& g, double alpha, const double* A, const double* B,
                 double* scratch, int scratch_len, double* out_slot, cudaStream_t st);
-void launch_gemm(const GemmArgs& g, cudaStream_t st);
+// kind 0: generic contraction, 1: DF build of (pr|qs), 2: ladder contraction
+void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind = 0);
 void launch_fill(double* p, long long n, double v, cudaStream_t st);
 
 // Reference quantities on spin orbitals.

@@ -257,9 +257,8 @@ def make_instance(nc: int, na: int, nel: int, nv: int, naux: int, s: float = 0.5
 
 def config_instance(name: str, **kw) -> dict:
     c = dict(CONFIGS[name])
-    seed = c.pop("seed")
     c.update(kw)
-    return make_instance(seed=seed, **c)
+    return make_instance(**c)
 
 
 def scan_instance(j: int, nscan: int = 32) -> dict:
