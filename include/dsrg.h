@@ -135,6 +135,24 @@ long long dsrg_last_d2h_bytes(const dsrg_handle *h);
 long long dsrg_peak_bytes(const dsrg_handle *h);
 
 /*
+ * Density-fitted particle-particle ladder on caller buffers (Eq.
+ * scaling_problem with the factorised integrals of Eq. int_fact): for
+ * p, q, r, s in [0, np) and i, j in [0, nh)
+ *   L[p][q][i][j] = sum_{r,s} (sum_Q B[Q][p0+p][p0+r] B[Q][p0+q][p0+s]) t[r][s][i][j]
+ * B: device [naux][n][n]; t: device [np][np][nh][nh]; L: device
+ * [np][np][nh][nh], overwritten.  All FP64, row-major, device memory of the
+ * current GPU; stream may be NULL (legacy default stream).  With t the
+ * alpha-beta block of the spin-free first-order amplitudes this is the
+ * spatial ladder from which the energy driver assembles all spin blocks.
+ * The (pr|qs) rows are formed in batches in a scratch buffer of at most
+ * 1 GiB obtained with cudaMalloc and released before return; the call
+ * synchronises `stream`.  Errors: DSRG_ERR_ARG (sizes, p0 + np > n, NULL
+ * pointers), DSRG_ERR_OOM (scratch), DSRG_ERR_CUDA.
+ */
+int dsrg_df_ladder(int n, int naux, int p0, int np, int nh, const double *B, const double *t, double *L,
+                   void *stream);
+
+/*
  * Intermediate access for testing.  Copies a named spin-orbital tensor of the
  * last dsrg_pt2/dsrg_pt3 call to host memory `dst` (FP64, row-major) if its
  * element count equals `count`.  Names and layouts, with H = core+active

@@ -211,3 +211,13 @@ def dsrg_pt3(inst: dict, pt2_only: bool = False, eri=None, return_intermediates=
         out["_inter"] = inter
         out["_problem"] = P
     return out
+
+
+def df_ladder(B: np.ndarray, t: np.ndarray, p0: int) -> np.ndarray:
+    """Spatial particle-particle ladder of Eq. scaling_problem with the
+    integrals of Eq. int_fact: L[p,q,i,j] = sum_rs (p r|q s) t[r,s,i,j],
+    (p r|q s) = sum_Q B[Q,p0+p,p0+r] B[Q,p0+q,p0+s]."""
+    npart = t.shape[0]
+    Bp = B[:, p0:p0 + npart, p0:p0 + npart]
+    J = np.einsum("Qpr,Qqs->pqrs", Bp, Bp)
+    return np.einsum("pqrs,rsij->pqij", J, t)

@@ -44,7 +44,7 @@ class dsrg_energies(ctypes.Structure):
 
 EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_free", "dsrg_last_error",
            "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
-           "dsrg_last_d2h_bytes")
+           "dsrg_last_d2h_bytes", "dsrg_df_ladder")
 
 _lib = None
 
@@ -81,6 +81,8 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
     L.dsrg_profile_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                      ctypes.POINTER(ctypes.c_longlong), _P, _P, _P]
     L.dsrg_profile_stats.restype = ctypes.c_int
+    L.dsrg_df_ladder.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 4
+    L.dsrg_df_ladder.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -215,6 +217,20 @@ def dsrg_fetch(h, name: str, nc: int, na: int, nv: int) -> np.ndarray:
     out = np.empty(shape, dtype=np.float64)
     _check(load_library().dsrg_fetch(h, name.encode(), out.ctypes.data_as(_P), int(out.size)))
     return out
+
+
+def _dev_ptr(x):
+    if not (hasattr(x, "is_cuda") and x.is_cuda and x.element_size() == 8 and x.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def dsrg_df_ladder(B, t, L, p0: int, stream=None) -> None:
+    """L[p,q,i,j] = sum_rs (sum_Q B[Q,p0+p,p0+r] B[Q,p0+q,p0+s]) t[r,s,i,j] on CUDA tensors."""
+    naux, n, _ = B.shape
+    np_, _, nh, _ = t.shape
+    _check(load_library().dsrg_df_ladder(n, naux, p0, np_, nh, _dev_ptr(B), _dev_ptr(t), _dev_ptr(L),
+                                         ctypes.c_void_p(stream) if stream else None))
 
 
 class Dsrg:

@@ -120,6 +120,10 @@ void load_inputs(dsrg::Handle& h, const dsrg_inputs* in) {
 }
 }  // namespace
 
+namespace dsrg {
+int set_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
+}  // namespace dsrg
+
 extern "C" {
 
 const char* dsrg_last_error(void) { return g_last_error.c_str(); }

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "dsrg_impl.cuh"
+#include "ladder.cuh"
 
 namespace dsrg {
 
@@ -180,7 +181,6 @@ void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tenso
 // 1/2 sum_rs <pq||rs> T2[r,s,i,j] follow from L (Eq. scaling_problem).
 void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
   const int p = h.na + h.nv, hh = h.nc + h.na;
-  const long long n = h.n;
   if (p == 0 || hh == 0) return;
   const View& tv = T2.v;
   const double* t = tv.p + tv.ss[1] + tv.ss[3];
@@ -189,56 +189,12 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
   double* L = h.ws.get(nL, capL);
   check_cuda(cudaMemsetAsync(L, 0, nL * sizeof(double), h.ws.stream), "memset");
   const long long p3 = (long long)p * p * p;
-  long long bp = (1LL << 27) / (p3 > 0 ? p3 : 1);  // <= 1 GiB of (pr|qs) per batch
+  long long bp = ladder_batch_rows(p, 1LL << 27);  // <= 1 GiB of (pr|qs) per batch
   if (bp < 1) bp = 1;
-  if (bp > p) bp = p;
   size_t capG;
   double* G = h.ws.get((size_t)(bp * p3), capG);
-  for (long long p0 = 0; p0 < p; p0 += bp) {
-    long long nb = (p - p0 < bp) ? p - p0 : bp;
-    check_cuda(cudaMemsetAsync(G, 0, (size_t)(nb * p3) * sizeof(double), h.ws.stream), "memset");
-    {  // G[pp,q,r,s] = sum_Q B[Q,P0+p0+pp,P0+r] B[Q,P0+q,P0+s]
-      GemmArgs g{};
-      g.A = h.B + (h.nc + p0) * n + h.nc;
-      g.B = h.B + h.nc * n + h.nc;
-      g.C = G;
-      g.alpha = 1.0;
-      g.nM = 2;
-      g.eM[0] = (int)nb; g.aM[0] = n; g.cM[0] = p3;
-      g.eM[1] = p;       g.aM[1] = 1; g.cM[1] = p;
-      g.nN = 2;
-      g.eN[0] = p; g.bN[0] = n; g.cN[0] = (long long)p * p;
-      g.eN[1] = p; g.bN[1] = 1; g.cN[1] = 1;
-      g.nK = 1;
-      g.eK[0] = h.naux; g.aK[0] = n * n; g.bK[0] = n * n;
-      g.M = nb * p;
-      g.N = (long long)p * p;
-      g.K = h.naux;
-      g.nbatch = 1;
-      run_gemm(h.ws, g, K_LADDER_BUILD);
-    }
-    {  // L[p0+pp,q,i,j] += sum_{r,s} G[pp,q,r,s] t[r,s,i,j]
-      GemmArgs g{};
-      g.A = G;
-      g.B = t;
-      g.C = L + p0 * (long long)p * hh * hh;
-      g.alpha = 1.0;
-      g.nM = 2;
-      g.eM[0] = (int)nb; g.aM[0] = p3;              g.cM[0] = (long long)p * hh * hh;
-      g.eM[1] = p;       g.aM[1] = (long long)p * p; g.cM[1] = (long long)hh * hh;
-      g.nK = 2;
-      g.eK[0] = p; g.aK[0] = p; g.bK[0] = tv.st[0];
-      g.eK[1] = p; g.aK[1] = 1; g.bK[1] = tv.st[1];
-      g.nN = 2;
-      g.eN[0] = hh; g.bN[0] = tv.st[2]; g.cN[0] = hh;
-      g.eN[1] = hh; g.bN[1] = tv.st[3]; g.cN[1] = 1;
-      g.M = nb * p;
-      g.N = (long long)hh * hh;
-      g.K = (long long)p * p;
-      g.nbatch = 1;
-      run_gemm(h.ws, g, K_LADDER_CONTRACT);
-    }
-  }
+  const long long tst[4] = {tv.st[0], tv.st[1], tv.st[2], tv.st[3]};
+  ladder_core(h.B, h.n, h.naux, h.nc, p, hh, t, tst, L, G, bp, h.ws.stream, &h.ws);
   h.ws.put(G, capG);
   // scatter into the spin blocks of C2 [2p][2p][2h][2h]
   const View& c = C2.v;

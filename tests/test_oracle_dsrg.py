@@ -367,3 +367,22 @@ def test_first_order_htilde_matches_printed_blocks():
     Ht1_2 = 2 * P.V + W.z[2]
     printed_2 = P.V * (1 + np.exp(-s * P.D2 ** 2))
     assert np.abs((Ht1_2 - printed_2)[P.mask2]).max() < 1e-12
+
+
+def test_df_ladder_definition_by_loops():
+    """The oracle's ladder definition against explicit loops on a tiny case."""
+    rng = np.random.default_rng(8)
+    naux, n, p0, npart, nh = 3, 5, 1, 4, 2
+    B = rng.standard_normal((naux, n, n))
+    t = rng.standard_normal((npart, npart, nh, nh))
+    L = dsrg.df_ladder(B, t, p0)
+    for p in range(npart):
+        for q in range(npart):
+            for i in range(nh):
+                for j in range(nh):
+                    acc = 0.0
+                    for r in range(npart):
+                        for s in range(npart):
+                            v = sum(B[Q, p0 + p, p0 + r] * B[Q, p0 + q, p0 + s] for Q in range(naux))
+                            acc += v * t[r, s, i, j]
+                    assert abs(L[p, q, i, j] - acc) < 1e-12 * max(1.0, abs(acc))
