@@ -153,6 +153,24 @@ int dsrg_df_ladder(int n, int naux, int p0, int np, int nh, const double *B, con
                    void *stream);
 
 /*
+ * dsrg_df_ladder without any device allocation (no counterpart in the paper:
+ * it serves callers that cannot call cudaMalloc, e.g. code running during
+ * CUDA stream capture or inside a framework that owns all device memory).
+ * Same arguments, contraction and result as dsrg_df_ladder.  The (pr|qs)
+ * rows live in one fixed file-scope device array of 2^22 doubles (32 MiB)
+ * that every GPU on which the library's device code is loaded holds until
+ * the process exits, so np^3 <= 2^22 (np <= 161) is required; larger np
+ * returns DSRG_ERR_ARG with a message.  The first call on a device looks up
+ * that array's device address (with the device current); make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents (each batch clears what it accumulates into);
+ * calls that overlap on the GPU (other streams, other host threads) race on
+ * it and must be serialised by the caller.  Synchronises `stream`.
+ */
+int dsrg_df_ladder_noalloc(int n, int naux, int p0, int np, int nh, const double *B, const double *t, double *L,
+                           void *stream);
+
+/*
  * Intermediate access for testing.  Copies a named spin-orbital tensor of the
  * last dsrg_pt2/dsrg_pt3 call to host memory `dst` (FP64, row-major) if its
  * element count equals `count`.  Names and layouts, with H = core+active

@@ -44,7 +44,7 @@ class dsrg_energies(ctypes.Structure):
 
 EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_free", "dsrg_last_error",
            "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
-           "dsrg_last_d2h_bytes", "dsrg_df_ladder")
+           "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc")
 
 _lib = None
 
@@ -83,6 +83,8 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
     L.dsrg_profile_stats.restype = ctypes.c_int
     L.dsrg_df_ladder.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 4
     L.dsrg_df_ladder.restype = ctypes.c_int
+    L.dsrg_df_ladder_noalloc.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 4
+    L.dsrg_df_ladder_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -231,6 +233,15 @@ def dsrg_df_ladder(B, t, L, p0: int, stream=None) -> None:
     np_, _, nh, _ = t.shape
     _check(load_library().dsrg_df_ladder(n, naux, p0, np_, nh, _dev_ptr(B), _dev_ptr(t), _dev_ptr(L),
                                          ctypes.c_void_p(stream) if stream else None))
+
+
+def dsrg_df_ladder_noalloc(B, t, L, p0: int, stream=None) -> None:
+    """dsrg_df_ladder without device allocation (fixed 32 MiB scratch, np <= 161);
+    for callers that cannot allocate, e.g. during stream capture."""
+    naux, n, _ = B.shape
+    np_, _, nh, _ = t.shape
+    _check(load_library().dsrg_df_ladder_noalloc(n, naux, p0, np_, nh, _dev_ptr(B), _dev_ptr(t), _dev_ptr(L),
+                                                 ctypes.c_void_p(stream) if stream else None))
 
 
 class Dsrg:
