@@ -96,27 +96,24 @@ Tensor vclass(Handle& h, const Iv* ivs, double coef) {
 // ---------------------------------------------------------------------------
 // operators X = c_v (f1 + V) + c_w W, with W given by its excitation blocks
 // ---------------------------------------------------------------------------
-void build_x(Handle& h, double c_v, const Tensor* W1, const Tensor* W2, double c_w, unsigned classes, Tensor& X1,
-             Sym2& X2) {
-  X1 = mk(h, {h.G, h.G});
+Tensor build_x1(Handle& h, double c_v, const Tensor* W1, double c_w) {
+  Tensor X1 = mk(h, {h.G, h.G});
   if (c_v != 0.0 && h.has_f1) axpy(h.ws, c_v, h.F1.v, "pq", X1, "pq");
   if (W1 && c_w != 0.0) {
     axpy(h.ws, c_w, W1->v, "ai", X1, "ai");
     axpy(h.ws, c_w, W1->v, "ai", X1, "ia");
   }
-  X2.cls.clear();
+  return X1;
+}
+
+// V on the canonical classes HHHH, HHHP, HHPP, PHPH, PPPH (bits 0..4)
+void build_v(Handle& h, unsigned classes, Sym2& V) {
+  V.cls.clear();
   const Iv& H = h.H;
   const Iv& P = h.P;
   Iv cl[5][4] = {{H, H, H, H}, {H, H, H, P}, {H, H, P, P}, {P, H, P, H}, {P, P, P, H}};
-  for (int c = 0; c < 5; ++c) {
-    if (!((classes >> c) & 1)) continue;
-    Tensor t = (c_v != 0.0) ? vclass(h, cl[c], c_v) : make_tensor(h.ws, 4, cl[c], true);
-    if (W2 && c_w != 0.0) {
-      axpy(h.ws, c_w, W2->v, "abcd", t, "abcd");
-      axpy(h.ws, c_w, W2->v, "cdab", t, "abcd");
-    }
-    X2.cls.push_back(std::move(t));
-  }
+  for (int c = 0; c < 5; ++c)
+    if ((classes >> c) & 1) V.cls.push_back(vclass(h, cl[c], 1.0));
 }
 
 Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M) {
@@ -218,8 +215,8 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
 // ---------------------------------------------------------------------------
 // [X, T] into one output block pair (C1, C2)
 // ---------------------------------------------------------------------------
-void commutator(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
-                Tensor& C2, bool df, const Tensor* Wpp, double c_wpp) {
+void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
+                Tensor& C2, bool df) {
   Workspace& ws = h.ws;
   const Tensor& g = h.gam;
   const Tensor& e = h.eta;
@@ -323,14 +320,12 @@ void commutator(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, c
   }
   // [X2, T2] two-body: particle ladder 1/2 X2 T2 - X2[p,q,r,b] (gamma T2)[r,b,i,j]
   if (exc) {
-    if (df) df_ladder(h, T2, C2, 1.0);
-    if (Wpp && c_wpp != 0.0 && h.na > 0) {
-      // W's particle-particle block lives on [P,P,A,A] and its transpose
-      const Iv ppaa[4] = {P, P, A, A};
-      View wv = Wpp->v.sub(ppaa);
-      contract(ws, 0.5 * c_wpp, wv, "pqrs", T2.v, "rsij", C2, "pqij");
-      contract(ws, 0.5 * c_wpp, wv, "rspq", T2.v, "rsij", C2, "pqij");
+    // the V part of the all-particle block is never stored: DF ladder
+    if (X2.V && X2.cv != 0.0) {
+      if (!df) throw std::runtime_error("particle ladder of V needs the DF path");
+      df_ladder(h, T2, C2, X2.cv);
     }
+    contract_x2(ws, 0.5, X2, "pqrs", T2.v, "rsij", C2, "pqij", true);
   } else {
     contract_x2(ws, 0.5, X2, "pqrs", T2.v, "rsij", C2, "pqij");
   }
@@ -345,11 +340,8 @@ void commutator(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, c
   {
     Iv xi = exc ? P : H, wi = exc ? H : P;
     Iv want[4] = {xi, H, P, wi};
-    View xv;
-    double sg;
-    if (!X2.resolve(want, xv, sg)) throw std::runtime_error("ring: two-body class missing");
     Tensor Xs = make_tensor(ws, 4, want, true);
-    axpy(ws, sg, xv, "abcd", Xs, "abcd");
+    fetch_x2(ws, 1.0, X2, Xs);
     Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
     Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
     Iv kiv[4] = {xi, P, H, wi};
@@ -364,12 +356,12 @@ void commutator(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, c
 }
 
 // excitation blocks of [X, T - T^+] = [X, T] + [X, T]^+ (X Hermitian)
-void commutator_A(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
-                  Tensor& O2, bool df, const Tensor* Wpp, double c_wpp) {
+void commutator_A(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
+                  Tensor& O2, bool df) {
   Tensor C1e = mk(h, {h.P, h.H}), C1d = mk(h, {h.H, h.P});
   Tensor C2e = mk(h, {h.P, h.P, h.H, h.H}), C2d = mk(h, {h.H, h.H, h.P, h.P});
-  commutator(h, X1, X2, T1, T2, C1e, C2e, df, Wpp, c_wpp);
-  commutator(h, X1, X2, T1, T2, C1d, C2d, df, Wpp, c_wpp);
+  commutator(h, X1, X2, T1, T2, C1e, C2e, df);
+  commutator(h, X1, X2, T1, T2, C1d, C2d, df);
   O1 = mk(h, {h.P, h.H});
   O2 = mk(h, {h.P, h.P, h.H, h.H});
   axpy(h.ws, 1.0, C1e.v, "ai", O1, "ai");
@@ -381,7 +373,7 @@ void commutator_A(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1,
 // ---------------------------------------------------------------------------
 // scalar <[X, T]>: only the X1[H,P] and X2[H,H,P,P] elements enter
 // ---------------------------------------------------------------------------
-void scalar(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2) {
+void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2) {
   Workspace& ws = h.ws;
   const Tensor& g = h.gam;
   const Tensor& e = h.eta;
@@ -501,10 +493,11 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   Tensor T1, T2, W1, W2;
   amplitudes(h, &F1ph, Vph, T1, T2, W1, W2);
   Vph.release();
-  // Htilde(1) = 2 H(1) + [H(0), A(1)] (Eq. Hbar_1st): E(2) needs its H,H,P,P class only
-  Tensor Xs1;
-  Sym2 Xs2;
-  build_x(h, 2.0, &W1, &W2, 1.0, 1u << 2, Xs1, Xs2);
+  // Htilde(1) = 2 H(1) + [H(0), A(1)] (Eq. Hbar_1st); V on the classes the terms need
+  Sym2 V;
+  build_v(h, pt3 ? 0x1fu : (1u << 2), V);
+  Tensor Xs1 = build_x1(h, 2.0, &W1, 1.0);
+  Op2 Xs2{&V, 2.0, &W2, 1.0};
   int r0 = ws.nresults;
   scalar(h, Xs1, Xs2, T1, T2);
   int r1 = ws.nresults;
@@ -519,24 +512,20 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   const Tensor& t1 = h.T1;
   const Tensor& t2 = h.T2;
   // O = 1/2 [Htilde(1), A(1)]_{1,2} = [H(1) + W/2, A(1)]_{1,2}
-  Tensor X1;
-  Sym2 X2;
-  build_x(h, 1.0, &W1, &W2, 0.5, 0x1f, X1, X2);
   Tensor O1, O2;
-  commutator_A(h, X1, X2, t1, t2, O1, O2, true, &W2, 0.5);
-  X2.cls.clear();
-  X1.release();
+  {
+    Tensor X1 = build_x1(h, 1.0, &W1, 0.5);
+    commutator_A(h, X1, Op2{&V, 1.0, &W2, 0.5}, t1, t2, O1, O2, true);
+  }
   // second-order amplitudes (Eqs. T1_2nd, T2_2nd) and [H(0), A(2)]
   Tensor U1, U2, V1, V2;
   amplitudes(h, &O1, O2, U1, U2, V1, V2);
   // [W, A(1)]_{1,2}
-  Tensor Y1;
-  Sym2 Y2;
-  build_x(h, 0.0, &W1, &W2, 1.0, 0x1f, Y1, Y2);
   Tensor Q1, Q2;
-  commutator_A(h, Y1, Y2, t1, t2, Q1, Q2, false, &W2, 1.0);
-  Y2.cls.clear();
-  Y1.release();
+  {
+    Tensor Y1 = build_x1(h, 0.0, &W1, 1.0);
+    commutator_A(h, Y1, Op2{nullptr, 0.0, &W2, 1.0}, t1, t2, Q1, Q2, false);
+  }
   // Htilde(2)_{1,2} excitation blocks = [H0, A(2)] + O - [W, A(1)] / 6
   Tensor Z1 = mk(h, {P, H}), Z2 = mk(h, {P, P, H, H});
   axpy(ws, 1.0, V1.v, "ai", Z1, "ai");
@@ -545,13 +534,11 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   axpy(ws, 1.0, V2.v, "abij", Z2, "abij");
   axpy(ws, 1.0, O2.v, "abij", Z2, "abij");
   axpy(ws, -1.0 / 6.0, Q2.v, "abij", Z2, "abij");
-  Tensor Zx1;
-  Sym2 Zx2;
-  build_x(h, 0.0, &Z1, &Z2, 1.0, 1u << 2, Zx1, Zx2);
+  Tensor Zx1 = build_x1(h, 0.0, &Z1, 1.0);
   int r2 = ws.nresults;
   scalar(h, Xs1, Xs2, U1, U2);
   int r3 = ws.nresults;
-  scalar(h, Zx1, Zx2, t1, t2);
+  scalar(h, Zx1, Op2{nullptr, 0.0, &Z2, 1.0}, t1, t2);
   int r4 = ws.nresults;
   *e3a = sum_results(h, r2, r3);
   *e3b = sum_results(h, r3, r4);

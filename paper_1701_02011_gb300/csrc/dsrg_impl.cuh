@@ -38,16 +38,16 @@ struct Handle {
 };
 
 Tensor vclass(Handle& h, const Iv* ivs, double coef);
-void build_x(Handle& h, double c_v, const Tensor* W1, const Tensor* W2, double c_w, unsigned classes, Tensor& X1,
-             Sym2& X2);
+Tensor build_x1(Handle& h, double c_v, const Tensor* W1, double c_w);
+void build_v(Handle& h, unsigned classes, Sym2& V);
 Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M);
 void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tensor& T2, Tensor& W1, Tensor& W2);
 void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef);
-void commutator(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
-                Tensor& C2, bool df, const Tensor* Wpp, double c_wpp);
-void commutator_A(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
-                  Tensor& O2, bool df, const Tensor* Wpp, double c_wpp);
-void scalar(Handle& h, const Tensor& X1, const Sym2& X2, const Tensor& T1, const Tensor& T2);
+void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
+                Tensor& C2, bool df);
+void commutator_A(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
+                  Tensor& O2, bool df);
+void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2);
 void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b);
 
 }  // namespace dsrg

@@ -79,11 +79,36 @@ void Workspace::prof_collect() {
   recs.clear();
 }
 
-void run_gemm(Workspace& ws, const GemmArgs& g, int kind) {
-  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nbatch <= 0) return;
+void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
+  if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0 || g0.nbatch <= 0) return;
+  GemmArgs g = g0;
+  // Few output tiles but a long contraction: split K over extra CTAs so the
+  // whole GPU works on it (partials reduced in a fixed order).
+  const long long tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64) * g.nbatch;
+  double* part = nullptr;
+  size_t cap = 0;
+  if (g.nbatch == 1 && tiles < 2 * 152 && g.K >= 1024) {
+    long long s = (4 * 152 + tiles - 1) / tiles;
+    if (s > g.K / 256) s = g.K / 256;
+    if (s > 4096) s = 4096;
+    const long long limit = (1LL << 25) / (g.M * g.N);
+    if (s > limit) s = limit;
+    if (s >= 2) {
+      long long kper = (g.K + s - 1) / s;
+      kper = (kper + 15) / 16 * 16;
+      s = (g.K + kper - 1) / kper;
+      if (s >= 2) {
+        part = ws.get((size_t)(s * g.M * g.N), cap);
+        g.splits = (int)s;
+        g.kper = kper;
+        g.part = part;
+      }
+    }
+  }
   int r = ws.begin(kind, 2.0 * (double)g.M * (double)g.N * (double)g.K * (double)g.nbatch, 0.0);
   launch_gemm(g, ws.stream, kind == K_LADDER_BUILD ? 1 : kind == K_LADDER_CONTRACT ? 2 : 0);
   ws.end(r);
+  if (part) ws.put(part, cap);  // stream order keeps later reuse behind the reduction
 }
 
 void run_axpy(Workspace& ws, const NdArgs& g, double alpha, const double* A, double* C) {
@@ -439,57 +464,94 @@ static void x2_request(const char* lx, const std::vector<Lab>& L, Iv* want) {
   }
 }
 
-bool contract_x2(Workspace& ws, double alpha, const Sym2& X, const char* lx, const View& B, const char* lb, Tensor& C,
-                 const char* lc, const Iv* extra_ivs, const char* extra_labs) {
+// W placed as an operator: identity on [P,P,H,H] or its Hermitian image
+static View w_place(const Tensor& W, int herm) {
+  static const int hp[4] = {2, 3, 0, 1};
+  if (!herm) return W.v;
+  View v;
+  v.rank = 4;
+  v.p = W.v.p;
+  for (int j = 0; j < 4; ++j) {
+    v.iv[j] = W.v.iv[hp[j]];
+    v.st[j] = W.v.st[hp[j]];
+    v.ss[j] = W.v.ss[hp[j]];
+  }
+  v.mask = 0;
+  for (int b = 0; b < 16; ++b) {
+    if (!((W.v.mask >> b) & 1)) continue;
+    int vb = 0;
+    for (int j = 0; j < 4; ++j) vb |= ((b >> hp[j]) & 1) << j;
+    v.mask |= 1ULL << vb;
+  }
+  return v;
+}
+
+static bool v_view(const Op2& X, const Iv* want, View& xv, double& sg, const char* what, bool skip) {
+  if (!X.V || X.cv == 0.0) return false;
+  for (int k = 0; k < 4; ++k)
+    if (want[k].lo < -100000000) throw std::runtime_error(std::string("unconstrained two-body label in ") + what);
+  if (X.V->resolve(want, xv, sg)) return true;
+  if (skip) return false;
+  char buf[256];
+  snprintf(buf, sizeof buf, "no stored two-body class covers [%d,%d)x[%d,%d)x[%d,%d)x[%d,%d) for %s", want[0].lo,
+           want[0].hi, want[1].lo, want[1].hi, want[2].lo, want[2].hi, want[3].lo, want[3].hi, what);
+  throw std::runtime_error(buf);
+}
+
+bool contract_x2(Workspace& ws, double alpha, const Op2& X, const char* lx, const View& B, const char* lb, Tensor& C,
+                 const char* lc, bool skip_v) {
   std::vector<Lab> L;
   add_operand(L, B, lb, 1);
   add_operand(L, C.v, lc, 2);
-  if (extra_labs)
-    for (int i = 0; extra_labs[i]; ++i) {
-      int j = find_lab(L, extra_labs[i]);
-      L[j].iv = isect(L[j].iv, extra_ivs[i]);
-    }
   for (auto& l : L)
     if (l.iv.empty()) return false;
+  bool any = false;
   Iv want[4];
   x2_request(lx, L, want);
-  for (int k = 0; k < 4; ++k)
-    if (want[k].lo < -100000000) throw std::runtime_error(std::string("unconstrained two-body label in ") + lx);
   View xv;
   double sg;
-  if (!X.resolve(want, xv, sg)) {
-    char buf[256];
-    snprintf(buf, sizeof buf, "no stored two-body class covers [%d,%d)x[%d,%d)x[%d,%d)x[%d,%d) for %s", want[0].lo,
-             want[0].hi, want[1].lo, want[1].hi, want[2].lo, want[2].hi, want[3].lo, want[3].hi, lx);
-    throw std::runtime_error(buf);
-  }
-  return contract(ws, alpha * sg, xv, lx, B, lb, C, lc);
+  if (!skip_v && v_view(X, want, xv, sg, lx, false)) any |= contract(ws, alpha * X.cv * sg, xv, lx, B, lb, C, lc);
+  if (X.W && X.cw != 0.0)
+    for (int herm = 0; herm < 2; ++herm) any |= contract(ws, alpha * X.cw, w_place(*X.W, herm), lx, B, lb, C, lc);
+  return any;
 }
 
-bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la, const Sym2& X, const char* lx,
+bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la, const Op2& X, const char* lx,
                       Tensor& C, const char* lc) {
   std::vector<Lab> L;
   add_operand(L, A, la, 0);
   add_operand(L, C.v, lc, 2);
   for (auto& l : L)
     if (l.iv.empty()) return false;
+  bool any = false;
   Iv want[4];
   x2_request(lx, L, want);
-  for (int k = 0; k < 4; ++k)
-    if (want[k].lo < -100000000) throw std::runtime_error(std::string("unconstrained two-body label in ") + lx);
   View xv;
   double sg;
-  if (!X.resolve(want, xv, sg)) throw std::runtime_error(std::string("no stored two-body class for ") + lx);
-  return contract(ws, alpha * sg, A, la, xv, lx, C, lc);
+  if (v_view(X, want, xv, sg, lx, false)) any |= contract(ws, alpha * X.cv * sg, A, la, xv, lx, C, lc);
+  if (X.W && X.cw != 0.0)
+    for (int herm = 0; herm < 2; ++herm) any |= contract(ws, alpha * X.cw, A, la, w_place(*X.W, herm), lx, C, lc);
+  return any;
 }
 
-void dot_x2(Workspace& ws, double alpha, const Sym2& X, const Tensor& U) {
+void dot_x2(Workspace& ws, double alpha, const Op2& X, const Tensor& U) {
   for (int k = 0; k < 4; ++k)
     if (U.v.iv[k].empty()) return;
   View xv;
   double sg;
-  if (!X.resolve(U.v.iv, xv, sg)) throw std::runtime_error("no stored two-body class for a scalar term");
-  dot(ws, alpha * sg, xv, "pqrs", U.v, "pqrs");
+  if (v_view(X, U.v.iv, xv, sg, "scalar term", false)) dot(ws, alpha * X.cv * sg, xv, "pqrs", U.v, "pqrs");
+  if (X.W && X.cw != 0.0)
+    for (int herm = 0; herm < 2; ++herm) dot(ws, alpha * X.cw, w_place(*X.W, herm), "pqrs", U.v, "pqrs");
+}
+
+void fetch_x2(Workspace& ws, double alpha, const Op2& X, Tensor& out) {
+  for (int k = 0; k < 4; ++k)
+    if (out.v.iv[k].empty()) return;
+  View xv;
+  double sg;
+  if (v_view(X, out.v.iv, xv, sg, "materialised class", false)) axpy(ws, alpha * X.cv * sg, xv, "abcd", out, "abcd");
+  if (X.W && X.cw != 0.0)
+    for (int herm = 0; herm < 2; ++herm) axpy(ws, alpha * X.cw, w_place(*X.W, herm), "abcd", out, "abcd");
 }
 
 }  // namespace dsrg

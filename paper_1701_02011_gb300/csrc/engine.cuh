@@ -116,12 +116,26 @@ struct Sym2 {
   bool resolve(const Iv* want, View& out, double& sign) const;
 };
 
-// C[lc] += alpha * X2[lx] * B[lb] with X2 served from the store.
-bool contract_x2(Workspace& ws, double alpha, const Sym2& X, const char* lx, const View& B, const char* lb,
-                 Tensor& C, const char* lc, const Iv* extra_lab_ivs = nullptr, const char* extra_labs = nullptr);
-bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la, const Sym2& X, const char* lx,
+// A two-body operator X2 = cv V + cw (W + W^+): V kept on complete canonical
+// classes, W given by its excitation block [P,P,H,H] (zero elsewhere), so
+// its Hermitian image occupies [H,H,P,P].
+struct Op2 {
+  const Sym2* V = nullptr;
+  double cv = 0.0;
+  const Tensor* W = nullptr;
+  double cw = 0.0;
+};
+
+// C[lc] += alpha * X2[lx] * B[lb].  With skip_v the V part is left out (the
+// caller evaluates it another way, e.g. the density-fitted ladder).
+bool contract_x2(Workspace& ws, double alpha, const Op2& X, const char* lx, const View& B, const char* lb,
+                 Tensor& C, const char* lc, bool skip_v = false);
+bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la, const Op2& X, const char* lx,
                       Tensor& C, const char* lc);
-void dot_x2(Workspace& ws, double alpha, const Sym2& X, const Tensor& U);
+// alpha * sum X2[pqrs] U[pqrs] over U's intervals
+void dot_x2(Workspace& ws, double alpha, const Op2& X, const Tensor& U);
+// out[abcd] += alpha * X2[abcd] on out's intervals
+void fetch_x2(Workspace& ws, double alpha, const Op2& X, Tensor& out);
 
 void check_cuda(cudaError_t e, const char* what);
 

@@ -37,7 +37,10 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
   const long long m0 = (long long)blockIdx.x * BM;
   const long long n0 = (long long)blockIdx.y * BN;
   long long oAb = 0, oBb = 0, oCb = 0;
-  {
+  const int split = g.splits > 1 ? (int)blockIdx.z : 0;
+  const long long kbeg = g.splits > 1 ? (long long)split * g.kper : 0;
+  const long long kend = g.splits > 1 ? (kbeg + g.kper < g.K ? kbeg + g.kper : g.K) : g.K;
+  if (g.splits <= 1) {
     long long lin = blockIdx.z;
     for (int d = g.nB - 1; d >= 0; --d) {
       long long q = lin / g.eB[d];
@@ -65,10 +68,10 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-  for (long long k0 = 0; k0 < g.K; k0 += BK) {
+  for (long long k0 = kbeg; k0 < kend; k0 += BK) {
     if (tid < BK) {
       long long k = k0 + tid;
-      if (k < g.K) decode(k, g.nK, g.eK, g.aK, g.bK, offAk[tid], offBk[tid]);
+      if (k < kend) decode(k, g.nK, g.eK, g.aK, g.bK, offAk[tid], offBk[tid]);
       else { offAk[tid] = -1; offBk[tid] = -1; }
     }
     __syncthreads();
@@ -99,6 +102,20 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
     }
     __syncthreads();
   }
+  if (g.splits > 1) {
+    double* P = g.part + (long long)split * g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      long long m = m0 + ty + 16 * i;
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        long long n = n0 + tx + 16 * j;
+        if (n < g.N) P[m * g.N + n] = acc[i][j];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     long long om = offCm[ty + 16 * i];
@@ -109,6 +126,21 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
       if (on < 0) continue;
       g.C[oCb + om + on] += g.alpha * acc[i][j];
     }
+  }
+}
+
+// C[m, n] += alpha * sum_z part[z][m][n], z in increasing order
+__global__ void k_gemm_splitk_reduce(const GemmArgs g) {
+  const long long MN = g.M * g.N;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < MN;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long m = idx / g.N, n = idx - m * g.N;
+    double s = 0.0;
+    for (int z = 0; z < g.splits; ++z) s += g.part[z * MN + idx];
+    long long oa, om, ob, on;
+    decode(m, g.nM, g.eM, g.aM, g.cM, oa, om);
+    decode(n, g.nN, g.eN, g.bN, g.cN, ob, on);
+    g.C[om + on] += g.alpha * s;
   }
 }
 
@@ -351,12 +383,14 @@ inline int grid_for(long long n, int threads, int cap = 152 * 16) {
 
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nbatch <= 0) return;
-  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)g.nbatch);
+  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
+            (unsigned)(g.splits > 1 ? g.splits : g.nbatch));
   switch (kind) {
     case 1: k_gemm<1><<<grid, NT, 0, st>>>(g); break;   // (pr|qs) build from B
     case 2: k_gemm<2><<<grid, NT, 0, st>>>(g); break;   // ladder contraction with T2
     default: k_gemm<0><<<grid, NT, 0, st>>>(g); break;  // every other contraction
   }
+  if (g.splits > 1) k_gemm_splitk_reduce<<<grid_for(g.M * g.N, 256), 256, 0, st>>>(g);
 }
 
 void launch_axpy(const NdArgs& g, double alpha, const double* A, double* C, cudaStream_t st) {

@@ -25,6 +25,12 @@ struct GemmArgs {
   long long bN[4], bK[4], bB[4];
   long long cM[4], cN[4], cB[4];
   long long M, N, K, nbatch;
+  // split-K (nbatch == 1 only): split z covers k in [z*kper, (z+1)*kper) and
+  // stores its partial tile densely in part[z][M][N]; a second kernel adds
+  // alpha * sum_z part[z] into C in a fixed order.
+  int splits;
+  long long kper;
+  double* part;
 };
 
 // Elementwise / reduction descriptor over an nd-dimensional index space.
