@@ -116,19 +116,40 @@ void build_v(Handle& h, unsigned classes, Sym2& V) {
     if ((classes >> c) & 1) V.cls.push_back(vclass(h, cl[c], 1.0));
 }
 
+// out[..z..] = sum_x M[z,x] X[..x..] along one slot, M = gamma (hole range)
+// or eta (particle range).  Both are the identity outside the active block
+// (gamma on core, eta on virtual), so the product is a copy there and a
+// small contraction with the active block.
 Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M) {
+  const int r = X.v.rank;
   Iv ivs[kMaxRank];
-  for (int k = 0; k < X.v.rank; ++k) ivs[k] = X.v.iv[k];
+  for (int k = 0; k < r; ++k) ivs[k] = X.v.iv[k];
   ivs[slot] = isect(M.v.iv[0], X.v.iv[slot]);
-  Tensor out = make_tensor(h.ws, X.v.rank, ivs, true);
+  Tensor out = make_tensor(h.ws, r, ivs, true);
+  if (ivs[slot].empty()) return out;
   char lx[8], lo[8], lm[3];
-  for (int k = 0; k < X.v.rank; ++k) lx[k] = lo[k] = "abcdef"[k];
-  lx[X.v.rank] = lo[X.v.rank] = 0;
-  lo[slot] = 'z';
-  lm[0] = 'z';
-  lm[1] = lx[slot];
-  lm[2] = 0;
-  contract(h.ws, 1.0, M.v, lm, X.v, lx, out, lo);
+  for (int k = 0; k < r; ++k) lx[k] = lo[k] = "abcdef"[k];
+  lx[r] = lo[r] = 0;
+  // identity part: the slot's orbitals outside the active space
+  const Iv& sl = ivs[slot];
+  Iv parts[2] = {isect(sl, Iv{sl.lo, h.A.lo}), isect(sl, Iv{h.A.hi, sl.hi})};
+  for (const Iv& part : parts) {
+    if (part.empty()) continue;
+    Iv sub[kMaxRank];
+    for (int k = 0; k < r; ++k) sub[k] = ivs[k];
+    sub[slot] = part;
+    View xv = X.v.sub(sub);
+    axpy(h.ws, 1.0, xv, lx, out, lx);
+  }
+  // active block
+  if (h.na > 0 && !isect(sl, h.A).empty()) {
+    const Iv aa[2] = {h.A, h.A};
+    lo[slot] = 'z';
+    lm[0] = 'z';
+    lm[1] = lx[slot];
+    lm[2] = 0;
+    contract(h.ws, 1.0, M.v.sub(aa), lm, X.v, lx, out, lo);
+  }
   return out;
 }
 
@@ -336,18 +357,41 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   // hole ladder
   contract_x2(ws, 0.5, X2, "pqrs", Ehh.v, "abpq", C2, "abrs");
   contract_x2(ws, -0.5, X2, "pqrs", Nhh.v, "abpq", C2, "abrs");
-  // ring: K[x,y,u,w] = sum_{i,a} (Xbar - Xtilde)[x,i,a,w] T2[a,y,i,u], antisymmetrised
+  // ring: K[x,y,u,w] = sum_{i,a} (Xbar - Xtilde)[x,i,a,w] T2[a,y,i,u], antisymmetrised.
+  // X2 is taken piece by piece (V, then W and its Hermitian image on their
+  // own boxes) so that no work is spent where a piece vanishes.
   {
     Iv xi = exc ? P : H, wi = exc ? H : P;
     Iv want[4] = {xi, H, P, wi};
-    Tensor Xs = make_tensor(ws, 4, want, true);
-    fetch_x2(ws, 1.0, X2, Xs);
-    Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
-    Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
-    Iv kiv[4] = {xi, P, H, wi};
+    // y and u must land in C2's slots as well as in T2's
+    Iv kiv[4] = {xi, isect(P, C2.v.iv[1]), isect(H, C2.v.iv[2]), wi};
     Tensor K = make_tensor(ws, 4, kiv, true);
-    contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
-    contract(ws, -1.0, Xt.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+    auto ring_piece = [&](const Tensor& Xs) {
+      Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
+      Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
+      contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+      contract(ws, -1.0, Xt.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+    };
+    if (X2.V && X2.cv != 0.0) {
+      Tensor Xs = make_tensor(ws, 4, want, true);
+      fetch_x2(ws, 1.0, Op2{X2.V, X2.cv, nullptr, 0.0}, Xs);
+      ring_piece(Xs);
+    }
+    if (X2.W && X2.cw != 0.0) {
+      for (int herm = 0; herm < 2; ++herm) {
+        View wp = w_place(*X2.W, herm);
+        Iv box[4];
+        bool empty = false;
+        for (int k = 0; k < 4; ++k) {
+          box[k] = isect(want[k], wp.iv[k]);
+          empty |= box[k].empty();
+        }
+        if (empty) continue;
+        Tensor Xs = make_tensor(ws, 4, box, true);
+        axpy(ws, X2.cw, wp, "abcd", Xs, "abcd");
+        ring_piece(Xs);
+      }
+    }
     axpy(ws, 1.0, K.v, "xyuw", C2, "xyuw");
     axpy(ws, -1.0, K.v, "xyuw", C2, "yxuw");
     axpy(ws, -1.0, K.v, "xyuw", C2, "xywu");

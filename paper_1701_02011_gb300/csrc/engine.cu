@@ -2,6 +2,8 @@
 #include "engine.cuh"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <stdexcept>
 
@@ -46,7 +48,7 @@ void Workspace::prof_reset() {
 int Workspace::begin(int id, double flops, double bytes) {
   launches++;
   if (!profiling) return -1;
-  Rec r{id, nullptr, nullptr, flops, bytes};
+  Rec r{id, nullptr, nullptr, flops, bytes, 0, 0, 0};
   for (cudaEvent_t* e : {&r.a, &r.b}) {
     if (!ev_pool.empty()) {
       *e = ev_pool.back();
@@ -66,6 +68,22 @@ void Workspace::end(int rec) {
 }
 
 void Workspace::prof_collect() {
+  // DSRG_PROFILE_TOP=n prints the n slowest contractions of the call (stderr)
+  const char* top = getenv("DSRG_PROFILE_TOP");
+  std::vector<std::pair<float, int>> order;
+  for (int i = 0; i < (int)recs.size(); ++i) {
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, recs[i].a, recs[i].b), "cudaEventElapsedTime");
+    order.push_back({ms, i});
+  }
+  if (top && atoi(top) > 0) {
+    std::sort(order.begin(), order.end(), [](auto& x, auto& y) { return x.first > y.first; });
+    for (int i = 0; i < (int)order.size() && i < atoi(top); ++i) {
+      const Rec& r = recs[order[i].second];
+      fprintf(stderr, "[dsrg] %-10s %9.3f ms  M=%lld N=%lld K=%lld  %.3f TFLOP/s\n", kernel_name(r.id),
+              order[i].first, r.m, r.n, r.k, r.flops / (order[i].first * 1e-3) / 1e12);
+    }
+  }
   for (auto& r : recs) {
     float ms = 0.f;
     check_cuda(cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
@@ -83,13 +101,33 @@ void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
   if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0 || g0.nbatch <= 0) return;
   GemmArgs g = g0;
   // Few output tiles but a long contraction: split K over extra CTAs so the
-  // whole GPU works on it (partials reduced in a fixed order).
-  const long long tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64) * g.nbatch;
+  // whole GPU works on it (partials reduced in a fixed order).  Tiny outputs
+  // go to the one-CTA-per-element kernel instead.
+  int bm = 64, bn = 64;
+  if (kind == K_GEMM) gemm_tile(g.M, g.N, &bm, &bn);
+  const long long tiles = ((g.M + bm - 1) / bm) * ((g.N + bn - 1) / bn) * g.nbatch;
   double* part = nullptr;
   size_t cap = 0;
-  if (g.nbatch == 1 && tiles < 2 * 152 && g.K >= 1024) {
+  const bool small = kind == K_GEMM && gemm_is_small(g);
+  const bool shortk = kind == K_GEMM && gemm_is_short(g);
+  if (small && g.nbatch == 1 && g.K >= 4096) {
+    // one CTA per output element: split K until the GPU is covered
+    long long outs = g.M * g.N;
+    long long s = (4 * 152 + outs - 1) / outs;
+    if (s > g.K / 2048) s = g.K / 2048;
+    if (s >= 2) {
+      long long kper = (g.K + s - 1) / s;
+      s = (g.K + kper - 1) / kper;
+      if (s >= 2) {
+        part = ws.get((size_t)(s * outs), cap);
+        g.splits = (int)s;
+        g.kper = kper;
+        g.part = part;
+      }
+    }
+  } else if (!small && !shortk && g.nbatch == 1 && tiles < 2 * 152 && g.K >= 64) {
     long long s = (4 * 152 + tiles - 1) / tiles;
-    if (s > g.K / 256) s = g.K / 256;
+    if (s > g.K / 32) s = g.K / 32;
     if (s > 4096) s = 4096;
     const long long limit = (1LL << 25) / (g.M * g.N);
     if (s > limit) s = limit;
@@ -106,6 +144,11 @@ void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
     }
   }
   int r = ws.begin(kind, 2.0 * (double)g.M * (double)g.N * (double)g.K * (double)g.nbatch, 0.0);
+  if (r >= 0) {
+    ws.recs[r].m = g.M;
+    ws.recs[r].n = g.N;
+    ws.recs[r].k = g.K * g.nbatch;
+  }
   launch_gemm(g, ws.stream, kind == K_LADDER_BUILD ? 1 : kind == K_LADDER_CONTRACT ? 2 : 0);
   ws.end(r);
   if (part) ws.put(part, cap);  // stream order keeps later reuse behind the reduction
@@ -465,7 +508,7 @@ static void x2_request(const char* lx, const std::vector<Lab>& L, Iv* want) {
 }
 
 // W placed as an operator: identity on [P,P,H,H] or its Hermitian image
-static View w_place(const Tensor& W, int herm) {
+View w_place(const Tensor& W, int herm) {
   static const int hp[4] = {2, 3, 0, 1};
   if (!herm) return W.v;
   View v;

@@ -76,7 +76,7 @@ class Workspace {
   long long launches = 0;
   // opt-in per-launch timing
   bool profiling = false;
-  struct Rec { int id; cudaEvent_t a, b; double flops, bytes; };
+  struct Rec { int id; cudaEvent_t a, b; double flops, bytes; long long m, n, k; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> ev_pool;
   long long prof_launches[K_NKERNELS] = {0};
@@ -136,6 +136,9 @@ bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la
 void dot_x2(Workspace& ws, double alpha, const Op2& X, const Tensor& U);
 // out[abcd] += alpha * X2[abcd] on out's intervals
 void fetch_x2(Workspace& ws, double alpha, const Op2& X, Tensor& out);
+// W placed as an operator: its excitation block (herm = 0) or the Hermitian
+// image of that block (herm = 1), as a view with permuted slots
+View w_place(const Tensor& W, int herm);
 
 void check_cuda(cudaError_t e, const char* what);
 

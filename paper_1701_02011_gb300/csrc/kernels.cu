@@ -28,14 +28,18 @@ __device__ __forceinline__ void decode(long long lin, int nd, const int* ext, co
   }
 }
 
-template <int TAG>
+// Tile BM_ x BN_ with 256 threads, each owning a 4 x 4 block of outputs at
+// rows tm + (BM_/4) i and columns tn + (BN_/4) j (conflict-free shared reads).
+template <int BM_, int BN_, int TAG>
 __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
-  __shared__ double As[BK][BM];
-  __shared__ double Bs[BK][BN];
-  __shared__ long long offAm[BM], offCm[BM], offBn[BN], offCn[BN], offAk[BK], offBk[BK];
+  constexpr int NTN = BN_ / 4, NTM = BM_ / 4;
+  static_assert(NTM * NTN == NT, "tile must give 256 threads 4x4 outputs each");
+  __shared__ double As[BK][BM_];
+  __shared__ double Bs[BK][BN_];
+  __shared__ long long offAm[BM_], offCm[BM_], offBn[BN_], offCn[BN_], offAk[BK], offBk[BK];
   const int tid = threadIdx.x;
-  const long long m0 = (long long)blockIdx.x * BM;
-  const long long n0 = (long long)blockIdx.y * BN;
+  const long long m0 = (long long)blockIdx.x * BM_;
+  const long long n0 = (long long)blockIdx.y * BN_;
   long long oAb = 0, oBb = 0, oCb = 0;
   const int split = g.splits > 1 ? (int)blockIdx.z : 0;
   const long long kbeg = g.splits > 1 ? (long long)split * g.kper : 0;
@@ -51,17 +55,17 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
       lin = q;
     }
   }
-  if (tid < BM) {
-    long long m = m0 + tid;
-    if (m < g.M) decode(m, g.nM, g.eM, g.aM, g.cM, offAm[tid], offCm[tid]);
-    else { offAm[tid] = -1; offCm[tid] = -1; }
-  } else if (tid < BM + BN) {
-    int t = tid - BM;
+  for (int t = tid; t < BM_; t += NT) {
+    long long m = m0 + t;
+    if (m < g.M) decode(m, g.nM, g.eM, g.aM, g.cM, offAm[t], offCm[t]);
+    else { offAm[t] = -1; offCm[t] = -1; }
+  }
+  for (int t = tid; t < BN_; t += NT) {
     long long n = n0 + t;
     if (n < g.N) decode(n, g.nN, g.eN, g.bN, g.cN, offBn[t], offCn[t]);
     else { offBn[t] = -1; offCn[t] = -1; }
   }
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tn = tid % NTN, tm = tid / NTN;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -76,14 +80,14 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
     }
     __syncthreads();
 #pragma unroll
-    for (int e = tid; e < BM * BK; e += NT) {
-      int mm = e % BM, kk = e / BM;
+    for (int e = tid; e < BM_ * BK; e += NT) {
+      int mm = e % BM_, kk = e / BM_;
       long long om = offAm[mm], ok = offAk[kk];
       As[kk][mm] = (om >= 0 && ok >= 0) ? g.A[oAb + om + ok] : 0.0;
     }
 #pragma unroll
-    for (int e = tid; e < BN * BK; e += NT) {
-      int nn = e % BN, kk = e / BN;
+    for (int e = tid; e < BN_ * BK; e += NT) {
+      int nn = e % BN_, kk = e / BN_;
       long long on = offBn[nn], ok = offBk[kk];
       Bs[kk][nn] = (on >= 0 && ok >= 0) ? g.B[oBb + on + ok] : 0.0;
     }
@@ -92,9 +96,9 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
     for (int kk = 0; kk < BK; ++kk) {
       double a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + NTM * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tn + NTN * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -103,29 +107,135 @@ __global__ void __launch_bounds__(NT) k_gemm(const GemmArgs g) {
     __syncthreads();
   }
   if (g.splits > 1) {
-    double* P = g.part + (long long)split * g.M * g.N;
+    double* Pp = g.part + (long long)split * g.M * g.N;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      long long m = m0 + ty + 16 * i;
+      long long m = m0 + tm + NTM * i;
       if (m >= g.M) continue;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        long long n = n0 + tx + 16 * j;
-        if (n < g.N) P[m * g.N + n] = acc[i][j];
+        long long n = n0 + tn + NTN * j;
+        if (n < g.N) Pp[m * g.N + n] = acc[i][j];
       }
     }
     return;
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    long long om = offCm[ty + 16 * i];
+    long long om = offCm[tm + NTM * i];
     if (om < 0) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      long long on = offCn[tx + 16 * j];
+      long long on = offCn[tn + NTN * j];
       if (on < 0) continue;
       g.C[oCb + om + on] += g.alpha * acc[i][j];
     }
+  }
+}
+
+// Outputs too few to fill tiles: one CTA per output element, its threads
+// split K (32-bit index decoding), fixed-order tree reduction.
+constexpr int SMALL_T = 128;
+__device__ __forceinline__ void decode32(int lin, int nd, const int* ext, const long long* s1, const long long* s2,
+                                         long long& o1, long long& o2) {
+  o1 = 0;
+  o2 = 0;
+  for (int d = nd - 1; d >= 0; --d) {
+    int q = lin / ext[d];
+    int r = lin - q * ext[d];
+    o1 += r * s1[d];
+    o2 += r * s2[d];
+    lin = q;
+  }
+}
+
+__global__ void __launch_bounds__(SMALL_T) k_gemm_small(const GemmArgs g) {
+  const long long out = blockIdx.x;  // over nbatch * M * N
+  const long long MN = g.M * g.N;
+  const long long b = out / MN, mn = out - b * MN;
+  const long long m = mn / g.N, n = mn - m * g.N;
+  long long oAb = 0, oBb = 0, oCb = 0;
+  {
+    long long lin = b;
+    for (int d = g.nB - 1; d >= 0; --d) {
+      long long q = lin / g.eB[d];
+      int r = (int)(lin - q * g.eB[d]);
+      oAb += r * g.aB[d];
+      oBb += r * g.bB[d];
+      oCb += r * g.cB[d];
+      lin = q;
+    }
+  }
+  long long oAm, oCm, oBn, oCn;
+  decode(m, g.nM, g.eM, g.aM, g.cM, oAm, oCm);
+  decode(n, g.nN, g.eN, g.bN, g.cN, oBn, oCn);
+  const double* A = g.A + oAb + oAm;
+  const double* B = g.B + oBb + oBn;
+  const int split = g.splits > 1 ? (int)blockIdx.y : 0;
+  const long long kb = g.splits > 1 ? split * g.kper : 0;
+  const long long ke = g.splits > 1 ? (kb + g.kper < g.K ? kb + g.kper : g.K) : g.K;
+  double acc = 0.0;
+  for (long long k = kb + threadIdx.x; k < ke; k += SMALL_T) {
+    long long oa, ob;
+    decode32((int)k, g.nK, g.eK, g.aK, g.bK, oa, ob);
+    acc = fma(A[oa], B[ob], acc);
+  }
+  __shared__ double sh[SMALL_T];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = SMALL_T / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (g.splits > 1) g.part[(long long)split * MN + mn] = sh[0];
+    else g.C[oCb + oCm + oCn] += g.alpha * sh[0];
+  }
+}
+
+// Short contractions (K <= 64): one thread per output element, the K-offset
+// table staged once per CTA in shared memory.
+constexpr int TPO_T = 256, TPO_KMAX = 64;
+__global__ void __launch_bounds__(TPO_T) k_gemm_tpo(const GemmArgs g, int mfast) {
+  __shared__ long long offA[TPO_KMAX], offB[TPO_KMAX];
+  const int K = (int)g.K;
+  for (int t = threadIdx.x; t < K; t += TPO_T) decode32(t, g.nK, g.eK, g.aK, g.bK, offA[t], offB[t]);
+  __syncthreads();
+  const long long total = g.M * g.N * g.nbatch;
+  for (long long idx = blockIdx.x * (long long)TPO_T + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * TPO_T) {
+    long long m, n, b;
+    if (mfast) {
+      long long r = idx / g.M;
+      m = idx - r * g.M;
+      b = r / g.N;
+      n = r - b * g.N;
+    } else {
+      long long r = idx / g.N;
+      n = idx - r * g.N;
+      b = r / g.M;
+      m = r - b * g.M;
+    }
+    long long oAb = 0, oBb = 0, oCb = 0;
+    {
+      long long lin = b;
+      for (int d = g.nB - 1; d >= 0; --d) {
+        long long q = lin / g.eB[d];
+        int rr = (int)(lin - q * g.eB[d]);
+        oAb += rr * g.aB[d];
+        oBb += rr * g.bB[d];
+        oCb += rr * g.cB[d];
+        lin = q;
+      }
+    }
+    long long oAm, oCm, oBn, oCn;
+    decode32((int)m, g.nM, g.eM, g.aM, g.cM, oAm, oCm);
+    decode32((int)n, g.nN, g.eN, g.bN, g.cN, oBn, oCn);
+    const double* A = g.A + oAb + oAm;
+    const double* B = g.B + oBb + oBn;
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) acc = fma(A[offA[k]], B[offB[k]], acc);
+    g.C[oCb + oCm + oCn] += g.alpha * acc;
   }
 }
 
@@ -381,15 +491,47 @@ inline int grid_for(long long n, int threads, int cap = 152 * 16) {
 }
 }  // namespace
 
+void gemm_tile(long long M, long long N, int* bm, int* bn) {
+  if (N <= 16) { *bm = 256; *bn = 16; }
+  else if (M <= 16) { *bm = 16; *bn = 256; }
+  else if (N <= 32) { *bm = 128; *bn = 32; }
+  else if (M <= 32) { *bm = 32; *bn = 128; }
+  else { *bm = 64; *bn = 64; }
+}
+
+bool gemm_is_small(const GemmArgs& g) { return g.M * g.N * g.nbatch <= 4096 && g.K < (1LL << 31); }
+
+bool gemm_is_short(const GemmArgs& g) {
+  return g.K <= TPO_KMAX && g.M < (1LL << 31) && g.N < (1LL << 31) && !gemm_is_small(g);
+}
+
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nbatch <= 0) return;
-  dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + BN - 1) / BN),
+  int bm, bn;
+  gemm_tile(g.M, g.N, &bm, &bn);
+  if (kind != 0) { bm = 64; bn = 64; }
+  dim3 grid((unsigned)((g.M + bm - 1) / bm), (unsigned)((g.N + bn - 1) / bn),
             (unsigned)(g.splits > 1 ? g.splits : g.nbatch));
-  switch (kind) {
-    case 1: k_gemm<1><<<grid, NT, 0, st>>>(g); break;   // (pr|qs) build from B
-    case 2: k_gemm<2><<<grid, NT, 0, st>>>(g); break;   // ladder contraction with T2
-    default: k_gemm<0><<<grid, NT, 0, st>>>(g); break;  // every other contraction
+  if (kind == 0 && gemm_is_small(g)) {
+    dim3 sg((unsigned)(g.M * g.N * g.nbatch), (unsigned)(g.splits > 1 ? g.splits : 1));
+    k_gemm_small<<<sg, SMALL_T, 0, st>>>(g);
+    if (g.splits > 1) k_gemm_splitk_reduce<<<grid_for(g.M * g.N, 256), 256, 0, st>>>(g);
+    return;
   }
+  if (kind == 0 && gemm_is_short(g)) {
+    // consecutive threads walk the output index whose operand stride is smallest
+    long long sm = g.nM ? (g.aM[g.nM - 1] < g.cM[g.nM - 1] ? g.aM[g.nM - 1] : g.cM[g.nM - 1]) : (1LL << 62);
+    long long sn = g.nN ? (g.bN[g.nN - 1] < g.cN[g.nN - 1] ? g.bN[g.nN - 1] : g.cN[g.nN - 1]) : (1LL << 62);
+    k_gemm_tpo<<<grid_for(g.M * g.N * g.nbatch, TPO_T, 152 * 32), TPO_T, 0, st>>>(g, sm < sn ? 1 : 0);
+    return;
+  }
+  if (kind == 1) k_gemm<64, 64, 1><<<grid, NT, 0, st>>>(g);        // (pr|qs) build from B
+  else if (kind == 2) k_gemm<64, 64, 2><<<grid, NT, 0, st>>>(g);   // ladder contraction with T2
+  else if (bn == 16) k_gemm<256, 16, 0><<<grid, NT, 0, st>>>(g);    // narrow outputs
+  else if (bm == 16) k_gemm<16, 256, 0><<<grid, NT, 0, st>>>(g);
+  else if (bn == 32) k_gemm<128, 32, 0><<<grid, NT, 0, st>>>(g);
+  else if (bm == 32) k_gemm<32, 128, 0><<<grid, NT, 0, st>>>(g);
+  else k_gemm<64, 64, 0><<<grid, NT, 0, st>>>(g);                   // every other contraction
   if (g.splits > 1) k_gemm_splitk_reduce<<<grid_for(g.M * g.N, 256), 256, 0, st>>>(g);
 }
 

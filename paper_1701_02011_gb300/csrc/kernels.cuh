@@ -47,6 +47,13 @@ void launch_axpy(const NdArgs& g, double alpha, const double* A, double* C, cuda
 // partial[slot] = alpha * sum A[idx] * B[idx]; deterministic two-pass reduction.
 void launch_dot(const NdArgs& g, double alpha, const double* A, const double* B,
                 double* scratch, int scratch_len, double* out_slot, cudaStream_t st);
+// Output tile of the generic contraction for an M x N output (kinds 1, 2
+// always use 64 x 64).
+void gemm_tile(long long M, long long N, int* bm, int* bn);
+// true when the output is small enough for one CTA per output element
+bool gemm_is_small(const GemmArgs& g);
+// true when K is short enough for one thread per output element
+bool gemm_is_short(const GemmArgs& g);
 // kind 0: generic contraction, 1: DF build of (pr|qs), 2: ladder contraction
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind = 0);
 void launch_fill(double* p, long long n, double v, cudaStream_t st);
