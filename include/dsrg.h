@@ -171,6 +171,24 @@ int dsrg_df_ladder_noalloc(int n, int naux, int p0, int np, int nh, const double
                            void *stream);
 
 /*
+ * Split-precision FP64 matrix product on the tensor cores (no counterpart in
+ * the paper: it is the contraction primitive of the mixed-precision path):
+ *   C[m][n] += alpha * sum_k A[m][k] B[k][n]
+ * A [M][K] (row stride lda), B [K][N] (row stride ldb), C [M][N] (row stride
+ * ldc), all FP64 device memory, row-major.  Every row of A and column of B is
+ * scaled by a power of two and cut into `slices` (1..7) signed 7-bit digits
+ * held exactly in BF16; digit products are accumulated exactly in FP32 over
+ * 64-long chunks of k by tcgen05.mma and added into a two-float running sum,
+ * so the result carries about 7*slices bits relative to the product of the
+ * row and column maxima (Ozaki et al., Numer. Algorithms 59 (2012) 95).
+ * Scratch is allocated and released inside the call; synchronises `stream`.
+ * Errors: DSRG_ERR_ARG (sizes >= 2^31, slices, NULL), DSRG_ERR_CUDA (launch
+ * failure, or a bounded wait inside the kernel ran out).
+ */
+int dsrg_split_gemm(long long M, long long N, long long K, const double *A, long long lda, const double *B,
+                    long long ldb, double *C, long long ldc, double alpha, int slices, void *stream);
+
+/*
  * Intermediate access for testing.  Copies a named spin-orbital tensor of the
  * last dsrg_pt2/dsrg_pt3 call to host memory `dst` (FP64, row-major) if its
  * element count equals `count`.  Names and layouts, with H = core+active

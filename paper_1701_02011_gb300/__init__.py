@@ -44,7 +44,7 @@ class dsrg_energies(ctypes.Structure):
 
 EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_free", "dsrg_last_error",
            "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
-           "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc")
+           "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc", "dsrg_split_gemm")
 
 _lib = None
 
@@ -85,6 +85,11 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
     L.dsrg_df_ladder.restype = ctypes.c_int
     L.dsrg_df_ladder_noalloc.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 4
     L.dsrg_df_ladder_noalloc.restype = ctypes.c_int
+    L.dsrg_split_gemm.argtypes = [ctypes.c_longlong] * 3 + [ctypes.c_void_p, ctypes.c_longlong,
+                                                            ctypes.c_void_p, ctypes.c_longlong,
+                                                            ctypes.c_void_p, ctypes.c_longlong,
+                                                            ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
+    L.dsrg_split_gemm.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -242,6 +247,20 @@ def dsrg_df_ladder_noalloc(B, t, L, p0: int, stream=None) -> None:
     np_, _, nh, _ = t.shape
     _check(load_library().dsrg_df_ladder_noalloc(n, naux, p0, np_, nh, _dev_ptr(B), _dev_ptr(t), _dev_ptr(L),
                                                  ctypes.c_void_p(stream) if stream else None))
+
+
+def dsrg_split_gemm(A, B, C, alpha: float = 1.0, slices: int = 6, stream=None) -> None:
+    """C += alpha A B (2-D CUDA float64 tensors, row-major, unit column stride) on the tensor cores."""
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2 and tuple(C.shape) == (M, N)
+    for x in (A, B, C):
+        if not (x.is_cuda and x.element_size() == 8 and x.stride(1) == 1):
+            raise ValueError("expected CUDA float64 matrices with unit column stride")
+    _check(load_library().dsrg_split_gemm(M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                                          ctypes.c_void_p(B.data_ptr()), B.stride(0),
+                                          ctypes.c_void_p(C.data_ptr()), C.stride(0), float(alpha), int(slices),
+                                          ctypes.c_void_p(stream) if stream else None))
 
 
 class Dsrg:

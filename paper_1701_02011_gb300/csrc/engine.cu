@@ -1,5 +1,6 @@
 // Host-side tensor machinery (see engine.cuh).
 #include "engine.cuh"
+#include "ozaki.cuh"
 
 #include <algorithm>
 #include <cstdio>
@@ -31,6 +32,8 @@ const char* kernel_name(int id) {
     case K_AXPY: return "k_axpy";
     case K_DOT: return "k_dot";
     case K_AMP: return "k_amp";
+    case K_OZAKI_PACK: return "k_ozaki_pack";
+    case K_OZAKI_MMA: return "k_ozaki_mma";
     default: return "?";
   }
 }
@@ -99,6 +102,10 @@ void Workspace::prof_collect() {
 
 void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
   if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0 || g0.nbatch <= 0) return;
+  if (ws.slices > 0 && g0.nbatch == 1 && g0.M >= 128 && g0.N >= 128 && g0.K >= 64) {
+    ozaki_gemm(ws, g0, ws.slices, kind == K_GEMM ? (int)K_OZAKI_MMA : kind);
+    return;
+  }
   GemmArgs g = g0;
   // Few output tiles but a long contraction: split K over extra CTAs so the
   // whole GPU works on it (partials reduced in a fixed order).  Tiny outputs

@@ -40,7 +40,7 @@ class Workspace;
 
 // Kernels whose launches can be timed one by one (opt-in) with CUDA events on
 // the launching stream.
-enum KernelId { K_GEMM = 0, K_LADDER_BUILD, K_LADDER_CONTRACT, K_AXPY, K_DOT, K_AMP, K_NKERNELS };
+enum KernelId { K_GEMM = 0, K_LADDER_BUILD, K_LADDER_CONTRACT, K_AXPY, K_DOT, K_AMP, K_OZAKI_PACK, K_OZAKI_MMA, K_NKERNELS };
 const char* kernel_name(int id);
 
 struct Tensor {
@@ -74,6 +74,9 @@ class Workspace {
   double* dot_scratch = nullptr;
   int dot_scratch_len = 0;
   long long launches = 0;
+  // > 0: large contractions run as split-precision tensor-core products with
+  // this many 7-bit digit slices per operand; 0: FP64 everywhere
+  int slices = 0;
   // opt-in per-launch timing
   bool profiling = false;
   struct Rec { int id; cudaEvent_t a, b; double flops, bytes; long long m, n, k; };

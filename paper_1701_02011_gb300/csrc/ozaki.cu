@@ -1,0 +1,554 @@
+// Split-precision FP64 contraction on tcgen05 (see ozaki.cuh).
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <stdexcept>
+
+#include "ozaki.cuh"
+
+namespace dsrg {
+namespace {
+
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64;
+constexpr int OZ_THREADS = 128;
+constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // 8192 bf16 = 16 KiB (A and B tiles alike)
+constexpr int OZ_TILE_BYTES = OZ_TILE_ELEMS * 2;
+constexpr uint32_t OZ_TMEM_COLS = 512;        // acc [0,128) hi [128,256) lo [256,384)
+constexpr long long OZ_WAIT_LIMIT = 1LL << 22;
+
+__device__ int g_oz_status;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzled
+// layout (rows of 64 bf16, 8-row groups 1024 bytes apart).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = 128, M = 128.
+constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                              ((uint32_t)(OZ_BM >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false if the phase did not complete in time
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  for (long long i = 0; i < OZ_WAIT_LIMIT; ++i)
+    if (mbar_try(bar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(OZ_IDESC), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+#define OZ_R32(a)                                                                                                   \
+  "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]),      \
+      "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]),        \
+      "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]),       \
+      "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31])
+#define OZ_W32(a)                                                                                                   \
+  "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]),    \
+      "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15]), "r"(a[16]), "r"(a[17]), "r"(a[18]),   \
+      "r"(a[19]), "r"(a[20]), "r"(a[21]), "r"(a[22]), "r"(a[23]), "r"(a[24]), "r"(a[25]), "r"(a[26]), "r"(a[27]),   \
+      "r"(a[28]), "r"(a[29]), "r"(a[30]), "r"(a[31])
+#define OZ_P32                                                                                                      \
+  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, " \
+  "%24, %25, %26, %27, %28, %29, %30, %31}"
+#define OZ_Q32                                                                                                      \
+  "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, "     \
+  "%24, %25, %26, %27, %28, %29, %30, %31, %32}"
+
+// 32 consecutive TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " OZ_P32 ", [%32];" : OZ_R32(r) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], " OZ_Q32 ";" ::"r"(taddr), OZ_W32(r) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+struct OzArgs {
+  const __nv_bfloat16* As;  // [S][MT][KT] tiles
+  const __nv_bfloat16* Bs;  // [S][NT][KT] tiles
+  const int* ea;            // [MT*128]
+  const int* fb;            // [NT*128]
+  int S, MT, NT, KT;
+  long long M, N;
+  double alpha;
+  double* C;
+  // C offsets: row m -> decoded with (nM, eM, cM), column n -> (nN, eN, cN)
+  int nM, nN;
+  int eM[4], eN[4];
+  long long cM[4], cN[4];
+  int* status;
+};
+
+__device__ __forceinline__ long long c_offset(long long lin, int nd, const int* ext, const long long* st) {
+  long long o = 0;
+  for (int d = nd - 1; d >= 0; --d) {
+    long long q = lin / ext[d];
+    o += (lin - q * ext[d]) * st[d];
+    lin = q;
+  }
+  return o;
+}
+
+// One CTA: a 128 x 128 tile of C.  Thread t owns TMEM lane t (tile row t).
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
+  extern __shared__ unsigned char oz_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + (size_t)a.S * OZ_TILE_BYTES;
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ long long colC[OZ_BN];
+  __shared__ int colE[OZ_BN];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int mt = blockIdx.x, nt = blockIdx.y;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int t = tid; t < OZ_BN; t += OZ_THREADS) {
+    long long n = (long long)nt * OZ_BN + t;
+    colC[t] = n < a.N ? c_offset(n, a.nN, a.eN, a.cN) : -1;
+    colE[t] = a.fb[(long long)nt * OZ_BN + t];
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm = tmem_base;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+
+  // zero the running float-float sums (hi, lo)
+  {
+    uint32_t z[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) z[q] = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tmem_st32(tm + lane_off + 128 + 32 * j, z);
+    tmem_wait_st();
+  }
+  uint32_t phase = 0;
+  bool ok = true;
+  const int S = a.S;
+  for (int kt = 0; kt < a.KT && ok; ++kt) {
+    // stage the S digit tiles of A and of B for this k chunk
+    for (int s = 0; s < S; ++s) {
+      const uint4* gA = (const uint4*)(a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS);
+      const uint4* gB = (const uint4*)(a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * OZ_TILE_ELEMS);
+      uint4* dA = (uint4*)(sA + (size_t)s * OZ_TILE_BYTES);
+      uint4* dB = (uint4*)(sB + (size_t)s * OZ_TILE_BYTES);
+      for (int i = tid; i < OZ_TILE_BYTES / 16; i += OZ_THREADS) {
+        dA[i] = gA[i];
+        dB[i] = gB[i];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    for (int c = 2; c <= S + 1 && ok; ++c) {
+      if (tid == 0) {
+        uint32_t accum = 0;
+        const int t0 = c - S > 1 ? c - S : 1, t1 = c - 1 < S ? c - 1 : S;
+        for (int t = t0; t <= t1; ++t) {
+          const int u = c - t;
+          const uint32_t aA = smem_u32(sA + (size_t)(t - 1) * OZ_TILE_BYTES);
+          const uint32_t aB = smem_u32(sB + (size_t)(u - 1) * OZ_TILE_BYTES);
+#pragma unroll
+          for (int ks = 0; ks < OZ_BK / 16; ++ks) {
+            mma_bf16(tm, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), accum);
+            accum = 1;
+          }
+        }
+        mma_commit(&bar);
+      }
+      ok = mbar_wait(&bar, phase);
+      phase ^= 1;
+      ok = __syncthreads_and(ok) != 0;
+      tc_fence_after();
+      if (!ok) break;
+      // fold level c: (hi, lo) += acc * 2^(-7c), two-sum in FP32
+      const float scale = exp2f(-7.0f * (float)c);
+#pragma unroll 1
+      for (int j = 0; j < 4; ++j) {
+        uint32_t acc[32], hi[32], lo[32];
+        tmem_ld32(tm + lane_off + 32 * j, acc);
+        tmem_ld32(tm + lane_off + 128 + 32 * j, hi);
+        tmem_ld32(tm + lane_off + 256 + 32 * j, lo);
+        tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          float x = __uint_as_float(acc[q]) * scale;
+          float h = __uint_as_float(hi[q]);
+          float s_ = h + x;
+          float bp = s_ - h;
+          float err = (h - (s_ - bp)) + (x - bp);
+          float l = __uint_as_float(lo[q]) + err;
+          float s2 = s_ + l;
+          l = l - (s2 - s_);
+          hi[q] = __float_as_uint(s2);
+          lo[q] = __float_as_uint(l);
+        }
+        tmem_st32(tm + lane_off + 128 + 32 * j, hi);
+        tmem_st32(tm + lane_off + 256 + 32 * j, lo);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    }
+  }
+  // epilogue: C[m, n] += alpha * 2^(ea[m] + fb[n]) * (hi + lo)
+  if (ok) {
+    const long long m = (long long)mt * OZ_BM + tid;
+    const long long offm = m < a.M ? c_offset(m, a.nM, a.eM, a.cM) : -1;
+    const int em = a.ea[(long long)mt * OZ_BM + tid];
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      uint32_t hi[32], lo[32];
+      tmem_ld32(tm + lane_off + 128 + 32 * j, hi);
+      tmem_ld32(tm + lane_off + 256 + 32 * j, lo);
+      tmem_wait_ld();
+      if (offm >= 0) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const long long oc = colC[32 * j + q];
+          if (oc < 0) continue;
+          double v = (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]);
+          a.C[offm + oc] += a.alpha * ldexp(v, em + colE[32 * j + q]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(OZ_TMEM_COLS)
+                              : "memory");
+  if (!ok && tid == 0) atomicExch(a.status ? a.status : &g_oz_status, 1);
+}
+
+// ---------------------------------------------------------------------------
+// operand preparation
+// ---------------------------------------------------------------------------
+struct OzPack {
+  const double* src;
+  int nR, nK;
+  int eR[4], eK[4];
+  long long sR[4], sK[4];
+  long long R, K;      // logical sizes
+  int T, KT;           // tiles along rows (128 each) and k (64 each)
+  int S;
+};
+
+__device__ __forceinline__ long long src_offset(long long lin, int nd, const int* ext, const long long* st) {
+  long long o = 0;
+  for (int d = nd - 1; d >= 0; --d) {
+    long long q = lin / ext[d];
+    o += (lin - q * ext[d]) * st[d];
+    lin = q;
+  }
+  return o;
+}
+
+// e[r] = max over k of the binary exponent ex with |x| < 2^ex (frexp)
+__global__ void k_ozaki_exp(const OzPack p, int* e) {
+  const long long total = p.R * p.K;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / p.K, k = i - r * p.K;
+    const double x = p.src[src_offset(r, p.nR, p.eR, p.sR) + src_offset(k, p.nK, p.eK, p.sK)];
+    if (x == 0.0) continue;
+    const long long bits = __double_as_longlong(x);
+    const int be = (int)((bits >> 52) & 0x7FF);
+    atomicMax(&e[r], be ? be - 1022 : -1022);
+  }
+}
+
+__global__ void k_ozaki_fill_int(int* p, long long n, int v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// digits of every element (zero padding outside the logical matrix)
+__global__ void k_ozaki_pack(const OzPack p, const int* e, __nv_bfloat16* dst) {
+  const long long Rp = (long long)p.T * OZ_BM, Kp = (long long)p.KT * OZ_BK;
+  const long long total = Rp * Kp;
+  const int F = 7 * p.S;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / Kp, k = i - r * Kp;
+    double x = 0.0;
+    if (r < p.R && k < p.K) x = p.src[src_offset(r, p.nR, p.eR, p.sR) + src_offset(k, p.nK, p.eK, p.sK)];
+    unsigned long long v = 0;
+    bool neg = false;
+    if (x != 0.0) {
+      const long long bits = __double_as_longlong(x);
+      neg = bits < 0;
+      const int be = (int)((bits >> 52) & 0x7FF);
+      unsigned long long m = (unsigned long long)(bits & ((1LL << 52) - 1));
+      int E;
+      if (be) {
+        m |= 1ULL << 52;
+        E = be - 1075;
+      } else {
+        E = -1074;
+      }
+      const int sh = E + F - e[r];  // v = m 2^sh < 2^F
+      if (sh >= 0) v = sh < 12 ? (m << sh) : 0;
+      else v = (-sh) >= 64 ? 0 : (m >> (-sh));
+    }
+    const int tr = (int)(r / OZ_BM), rr = (int)(r % OZ_BM), tk = (int)(k / OZ_BK), kk = (int)(k % OZ_BK);
+    const int chunk = kk >> 3, j = kk & 7;
+    const long long within = (long long)rr * OZ_BK + ((chunk ^ (rr & 7)) << 3) + j;
+    for (int t = 1; t <= p.S; ++t) {
+      int d = (int)((v >> (7 * (p.S - t))) & 127ULL);
+      if (neg) d = -d;
+      const long long tile = ((long long)(t - 1) * p.T + tr) * p.KT + tk;
+      dst[tile * OZ_TILE_ELEMS + within] = __float2bfloat16_rn((float)d);
+    }
+  }
+}
+
+inline int oz_grid(long long n) {
+  long long b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)b;
+}
+
+int* oz_status_ptr() {
+  int* p = nullptr;
+  check_cuda(cudaGetSymbolAddress((void**)&p, g_oz_status), "cudaGetSymbolAddress (status)");
+  return p;
+}
+
+size_t oz_smem_bytes(int S) { return (size_t)2 * S * OZ_TILE_BYTES + 1024; }
+
+void oz_launch_mma(const OzArgs& a, int MT, int NT, cudaStream_t st) {
+  // at least 120 KiB so that one CTA (and one 512-column TMEM allocation)
+  // occupies an SM
+  size_t smem = oz_smem_bytes(a.S);
+  if (smem < 120 * 1024) smem = 120 * 1024;
+  check_cuda(cudaFuncSetAttribute(k_ozaki_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+             "cudaFuncSetAttribute (ozaki)");
+  k_ozaki_mma<<<dim3(MT, NT), OZ_THREADS, smem, st>>>(a);
+}
+}  // namespace
+
+const void* g_oz_status_alias() { return (const void*)&g_oz_status; }
+
+int ozaki_status(cudaStream_t st) {
+  int v = 0;
+  check_cuda(cudaMemcpyFromSymbolAsync(&v, g_oz_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st), "status");
+  check_cuda(cudaStreamSynchronize(st), "sync");
+  return v;
+}
+
+void ozaki_mma_raw(const void* As, const void* Bs, const int* ea, const int* fb, int S, long long M, long long N,
+                   int MT, int NT, int KT, double alpha, double* C, long long ldc, int* status, cudaStream_t st) {
+  OzArgs a{};
+  a.As = (const __nv_bfloat16*)As;
+  a.Bs = (const __nv_bfloat16*)Bs;
+  a.ea = ea;
+  a.fb = fb;
+  a.S = S;
+  a.MT = MT;
+  a.NT = NT;
+  a.KT = KT;
+  a.M = M;
+  a.N = N;
+  a.alpha = alpha;
+  a.C = C;
+  a.nM = 1;
+  a.eM[0] = (int)M;
+  a.cM[0] = ldc;
+  a.nN = 1;
+  a.eN[0] = (int)N;
+  a.cN[0] = 1;
+  a.status = status;
+  oz_launch_mma(a, MT, NT, st);
+}
+
+void ozaki_gemm(Workspace& ws, const GemmArgs& g, int S, int kind) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return;
+  if (g.nbatch != 1) throw std::runtime_error("split-precision contraction needs nbatch == 1");
+  if (S < 1 || S > kOzakiMaxSlices) throw std::runtime_error("split-precision slices must be 1..7");
+  const int MT = (int)((g.M + OZ_BM - 1) / OZ_BM), NT = (int)((g.N + OZ_BN - 1) / OZ_BN);
+  const int KT = (int)((g.K + OZ_BK - 1) / OZ_BK);
+  cudaStream_t st = ws.stream;
+  size_t capA, capB, capE;
+  const size_t nA = (size_t)S * MT * KT * OZ_TILE_ELEMS, nB = (size_t)S * NT * KT * OZ_TILE_ELEMS;
+  // bf16 buffers carved from double-sized workspace blocks
+  double* bufA = ws.get((nA + 3) / 4, capA);
+  double* bufB = ws.get((nB + 3) / 4, capB);
+  const size_t nE = (size_t)MT * OZ_BM + (size_t)NT * OZ_BN;
+  double* bufE = ws.get((nE + 1) / 2, capE);
+  int* ea = (int*)bufE;
+  int* fb = ea + (size_t)MT * OZ_BM;
+  OzPack pa{};
+  pa.src = g.A;
+  pa.nR = g.nM;
+  pa.nK = g.nK;
+  for (int d = 0; d < 4; ++d) {
+    pa.eR[d] = g.eM[d];
+    pa.sR[d] = g.aM[d];
+    pa.eK[d] = g.eK[d];
+    pa.sK[d] = g.aK[d];
+  }
+  pa.R = g.M;
+  pa.K = g.K;
+  pa.T = MT;
+  pa.KT = KT;
+  pa.S = S;
+  OzPack pb{};
+  pb.src = g.B;
+  pb.nR = g.nN;
+  pb.nK = g.nK;
+  for (int d = 0; d < 4; ++d) {
+    pb.eR[d] = g.eN[d];
+    pb.sR[d] = g.bN[d];
+    pb.eK[d] = g.eK[d];
+    pb.sK[d] = g.bK[d];
+  }
+  pb.R = g.N;
+  pb.K = g.K;
+  pb.T = NT;
+  pb.KT = KT;
+  pb.S = S;
+  int r = ws.begin(K_OZAKI_PACK, 0.0, 8.0 * (double)(g.M + g.N) * (double)g.K * 2.0);
+  k_ozaki_fill_int<<<oz_grid((long long)nE), 256, 0, st>>>(ea, (long long)nE, -2000);
+  k_ozaki_exp<<<oz_grid(g.M * g.K), 256, 0, st>>>(pa, ea);
+  k_ozaki_exp<<<oz_grid(g.N * g.K), 256, 0, st>>>(pb, fb);
+  k_ozaki_pack<<<oz_grid((long long)MT * OZ_BM * KT * OZ_BK), 256, 0, st>>>(pa, ea, (__nv_bfloat16*)bufA);
+  k_ozaki_pack<<<oz_grid((long long)NT * OZ_BN * KT * OZ_BK), 256, 0, st>>>(pb, fb, (__nv_bfloat16*)bufB);
+  ws.end(r);
+  ws.launches += 4;
+  OzArgs a{};
+  a.As = (const __nv_bfloat16*)bufA;
+  a.Bs = (const __nv_bfloat16*)bufB;
+  a.ea = ea;
+  a.fb = fb;
+  a.S = S;
+  a.MT = MT;
+  a.NT = NT;
+  a.KT = KT;
+  a.M = g.M;
+  a.N = g.N;
+  a.alpha = g.alpha;
+  a.C = g.C;
+  a.nM = g.nM;
+  a.nN = g.nN;
+  for (int d = 0; d < 4; ++d) {
+    a.eM[d] = g.eM[d];
+    a.cM[d] = g.cM[d];
+    a.eN[d] = g.eN[d];
+    a.cN[d] = g.cN[d];
+  }
+  a.status = nullptr;
+  // executed tensor-core flops: pairs with t + u <= S + 1, padded tiles
+  const double pairs = (double)S * (S + 1) / 2.0;
+  r = ws.begin(kind, 2.0 * pairs * (double)MT * OZ_BM * (double)NT * OZ_BN * (double)KT * OZ_BK, 0.0);
+  oz_launch_mma(a, MT, NT, st);
+  ws.end(r);
+  ws.put(bufA, capA);
+  ws.put(bufB, capB);
+  ws.put(bufE, capE);
+}
+
+}  // namespace dsrg
+
+// ---------------------------------------------------------------------------
+// C entry point
+// ---------------------------------------------------------------------------
+#include "../../include/dsrg.h"
+
+namespace dsrg {
+int set_error(int code, const char* msg);
+}
+
+extern "C" int dsrg_split_gemm(long long M, long long N, long long K, const double* A, long long lda, const double* B,
+                               long long ldb, double* C, long long ldc, double alpha, int slices, void* stream) {
+  using namespace dsrg;
+  if (M < 0 || N < 0 || K < 0 || M >= (1LL << 31) || N >= (1LL << 31) || K >= (1LL << 31))
+    return set_error(DSRG_ERR_ARG, "split gemm: sizes must be in [0, 2^31)");
+  if (slices < 1 || slices > kOzakiMaxSlices) return set_error(DSRG_ERR_ARG, "split gemm: slices must be 1..7");
+  if (M == 0 || N == 0 || K == 0) return DSRG_OK;
+  if (!A || !B || !C) return set_error(DSRG_ERR_ARG, "split gemm: NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    Workspace ws(st);
+    int zero = 0;
+    check_cuda(cudaMemcpyToSymbolAsync(g_oz_status_alias(), &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st),
+               "status reset");
+    GemmArgs g{};
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.alpha = alpha;
+    g.nM = 1;
+    g.eM[0] = (int)M;
+    g.aM[0] = lda;
+    g.cM[0] = ldc;
+    g.nN = 1;
+    g.eN[0] = (int)N;
+    g.bN[0] = 1;
+    g.cN[0] = 1;
+    g.nK = 1;
+    g.eK[0] = (int)K;
+    g.aK[0] = 1;
+    g.bK[0] = ldb;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.nbatch = 1;
+    ozaki_gemm(ws, g, slices, K_OZAKI_MMA);
+    check_cuda(cudaGetLastError(), "split gemm launch");
+    if (ozaki_status(st)) return set_error(DSRG_ERR_CUDA, "split gemm: a bounded wait in the kernel ran out");
+  } catch (const std::exception& e) {
+    return set_error(DSRG_ERR_CUDA, e.what());
+  }
+  return DSRG_OK;
+}

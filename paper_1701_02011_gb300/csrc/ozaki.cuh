@@ -1,0 +1,38 @@
+// Split-precision ("error-free slice") FP64 contraction on the tcgen05 tensor
+// cores, after Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication and
+// its applications" (Numer. Algorithms 59, 2012).
+//
+// Each row of A (and each column of B) is scaled by a power of two so that
+// its largest element is below one in magnitude, and cut into S signed
+// digits of 7 bits: x = 2^e * sum_t d_t 2^(-7t), |d_t| <= 127, each digit
+// exact in BF16.  Products of digits summed over 64 consecutive k stay below
+// 2^24 and are therefore exact in the FP32 accumulator of tcgen05.mma
+// kind::f16.  The pairs (t,u) of one level c = t + u are accumulated
+// together (still exact), levels c <= S + 1 are kept, and each level sum is
+// added into a float-float (two FP32) running sum in tensor memory.  The
+// result carries about 7 S bits relative to the row/column maxima.
+#pragma once
+#include "engine.cuh"
+
+namespace dsrg {
+
+constexpr int kOzakiMaxSlices = 7;
+
+// Error status of the last split-precision contraction kernel (device flag
+// set when a bounded wait runs out); 0 = ok.
+int ozaki_status(cudaStream_t st);
+// the status flag's symbol (for cudaMemcpyToSymbol)
+const void* g_oz_status_alias();
+
+// C[m,n] += alpha * sum_k A[m,k] B[k,n] for the multi-index contraction g
+// (nbatch must be 1) with `slices` digits per operand.  Scratch comes from ws.
+void ozaki_gemm(Workspace& ws, const GemmArgs& g, int slices, int kind);
+
+// Exact test helper: the same kernel on already-sliced inputs.
+//   As: [S][MT][KT][128][64] bf16 tiles (swizzled), Bs: [S][NT][KT][128][64]
+//   ea[Mpad], fb[Npad] power-of-two exponents; C[M][N] row-major (ldc).
+void ozaki_mma_raw(const void* As, const void* Bs, const int* ea, const int* fb, int S, long long M, long long N,
+                   int MT, int NT, int KT, double alpha, double* C, long long ldc, int* status, cudaStream_t st);
+
+}  // namespace dsrg

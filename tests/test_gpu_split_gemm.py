@@ -1,0 +1,48 @@
+"""Split-precision tensor-core product (dsrg_split_gemm) against exact and
+FP64 references."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_02011_gb300 import build
+    build.build()
+    import paper_1701_02011_gb300 as g
+    g.load_library()
+    return g
+
+
+def test_one_slice_is_exact_on_small_integers(lib):
+    """|a|, |b| <= 127: one 7-bit digit holds every element exactly, so the
+    product must be exact (ragged M, N, K across 128/128/64 tiles)."""
+    import torch
+    rng = np.random.default_rng(1)
+    M, N, K = 200, 150, 300
+    A = rng.integers(-127, 128, (M, K)).astype(np.float64)
+    B = rng.integers(-127, 128, (K, N)).astype(np.float64)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    lib.dsrg_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 1.0, 1)
+    assert np.array_equal(C.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("slices,tol", [(3, 1e-5), (6, 1e-11)])
+def test_many_slices_match_fp64(lib, slices, tol):
+    import torch
+    rng = np.random.default_rng(2)
+    M, N, K = 257, 131, 700
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-6, 6, (M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-6, 6, (1, N)))
+    ref = A @ B
+    bound = np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
+    C0 = rng.standard_normal((M, N))
+    C = torch.from_numpy(C0.copy()).cuda()
+    lib.dsrg_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, -0.5, slices)
+    err = np.abs(C.cpu().numpy() - (C0 - 0.5 * ref)) / bound
+    assert err.max() < tol
