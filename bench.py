@@ -37,6 +37,16 @@ WORKLOAD = "cas66_c10_v100_q400"
 # FP64 runs on the SM's FP64 FMA units (no tcgen05 FP64 kind): 152 SMs x
 # 2 FP64 FMA per clock per SM x 2 flop x 2.070 GHz maximum SM clock.
 FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def _measured_bf16():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["bf16_tflops"])
+    return 1900.0  # fallback figure
+
+
+MEASURED_BF16 = _measured_bf16()
 SAMPLE_WORKLOAD = "cas44_c2_v12_q60"
 
 
@@ -193,6 +203,37 @@ def alg_flops(inst):
     return {"ladder": h * (h + 1) * p ** 4, "build": Q * p * p * (p * p + 1)}
 
 
+def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, clocks=None):
+    """Warm up, then time `steps` PT3 energies (CUDA events on the library's
+    stream, L2 flushed before each step, per-kernel events inside)."""
+    prec = g.DSRG_PREC_SPLIT if precision == "split" else g.DSRG_PREC_FP64
+    h = g.Dsrg(dev, stream=stream.cuda_stream, precision=prec, slices=slices if precision == "split" else 0)
+    energies = None
+    for _ in range(max(warmup, 0)):
+        energies = h.pt3()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    h.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    launches = 0
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            starts[k].record(stream)
+        energies = h.pt3()
+        launches += h.launches
+        with torch.cuda.stream(stream):
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    stats = h.profile_stats()
+    h.profile(False)
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    return h, ms, energies, stats, launches, clk
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -212,36 +253,18 @@ def run_ours(args, rank, world, local_rank):
     dev = {k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
            for k, v in inst.items()}
     torch.cuda.synchronize()
-    h = g.Dsrg(dev, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    energies = None
-    for _ in range(max(args.warmup, 0)):
-        energies = h.pt3()
-    # ---- timed region: inputs resident on the device
+    other = "fp64" if args.precision == "split" else "split"
+    # comparison path first (untimed for the headline), then the headline path
+    h2, ms2, e_other, stats2, _, _ = _time_path(g, torch, dev, stream, flush, max(1, min(args.steps, 3)),
+                                                args.warmup, other, args.slices)
+    h2.close()
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    clk = ClockSampler(local_rank)
-    clk.start()
-    h.profile(True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    launches = 0
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-            starts[k].record(stream)
-        energies = h.pt3()
-        launches += h.launches
-        with torch.cuda.stream(stream):
-            ends[k].record(stream)
-    torch.cuda.synchronize()
+    h, ms, energies, stats, launches, clocks = _time_path(g, torch, dev, stream, flush, args.steps, args.warmup,
+                                                          args.precision, args.slices, ClockSampler(local_rank))
     if dist:
         dist.barrier()
-    clocks = clk.stop()
-    stats = h.profile_stats()
-    h.profile(False)
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_s = sum(ms) / 1000.0
     if dist:
         t = torch.tensor([total_s], device="cuda")
@@ -253,8 +276,7 @@ def run_ours(args, rank, world, local_rank):
     host = {}
     for k, v in inst.items():
         if isinstance(v, np.ndarray):
-            t = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-            host[k] = t.numpy()
+            host[k] = torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
         else:
             host[k] = v
     e2e_ms = []
@@ -265,44 +287,58 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h.load(host)
-        e = h.pt3()
+        h.pt3()
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
         d2h = g.dsrg_last_d2h_bytes(h.h) + 32
     e2e_value = world * 1000.0 / statistics.median(e2e_ms)
-    # ---- roofline of the dominant kernel
-    dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
-    fp64_peak = FP64_ALU_PEAK_TFLOPS
-    peak_src = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz"
+    h.close()
+    # ---- roofline of the dominant kernel (by device time)
+    dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
     af = alg_flops(inst)
-    name, st = dom
-    if name == "k_gemm<1>":
-        alg = af["build"] * args.steps
-        alg_note = "Q p^2 (p^2+1) per energy ((pr|qs) build, pair-swap symmetry)"
-    elif name == "k_gemm<2>":
-        alg = af["ladder"] * args.steps
-        alg_note = "h (h+1) p^4 per energy (ladder, i <= j)"
+    steps = args.steps
+    if dom_name == "k_gemm<1>":
+        alg, note = af["build"] * steps, "Q p^2 (p^2+1) per energy ((pr|qs) build, pair-swap symmetry)"
+    elif dom_name == "k_gemm<2>":
+        alg, note = af["ladder"] * steps, "h (h+1) p^4 per energy (ladder, i <= j)"
     else:
-        alg = st["flops"]
-        alg_note = "2 M N K summed over the kernel's contractions"
-    achieved = alg / (st["ms"] / 1000.0) / 1e12 if st["ms"] > 0 else 0.0
-    roofline = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None, "peak_source": peak_src,
-                "algorithmic": alg_note, "launches_per_step": st["launches"] / args.steps,
-                "avg_launch_ms": st["ms"] / max(1, st["launches"]),
-                "share_of_step": (st["ms"] / 1000.0) / max(total_s, 1e-30)}
+        alg, note = dom["flops"], "2 M N K summed over the kernel's contractions"
+    tensor_kernel = dom_name == "k_ozaki_mma"
+    peak = MEASURED_BF16 if tensor_kernel else FP64_ALU_PEAK_TFLOPS
+    achieved = alg / (dom["ms"] / 1000.0) / 1e12 if dom["ms"] > 0 else 0.0
+    roofline = {"kernel": dom_name, "bound": "tensor" if tensor_kernel else "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "of measured bf16 burst" if tensor_kernel else
+                "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz",
+                "algorithmic": note, "launches_per_step": dom["launches"] / steps,
+                "avg_launch_ms": dom["ms"] / max(1, dom["launches"]),
+                "share_of_step": (dom["ms"] / 1000.0) / max(total_s, 1e-30)}
+    tensor = stats.get("k_ozaki_mma", {"launches": 0, "ms": 0.0, "flops": 0.0})
+    roof_tensor = None
+    if tensor["launches"]:
+        executed = tensor["flops"] / (tensor["ms"] / 1000.0) / 1e12
+        roof_tensor = {"kernel": "k_ozaki_mma", "bound": "tensor", "achieved": executed, "peak": MEASURED_BF16,
+                       "unit": "TFLOP/s", "frac": executed / MEASURED_BF16,
+                       "note": "executed bf16 flops (digit-slice pairs and tile padding included) per device time",
+                       "launches_per_step": tensor["launches"] / steps,
+                       "share_of_step": (tensor["ms"] / 1000.0) / max(total_s, 1e-30)}
     eff_tflops = (af["ladder"] + af["build"]) * value / 1e12
+    err = {k: energies[k] - e_other[k] for k in ("e2", "e3a", "e3b", "e3")}
     line = {
         "metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; see DESIGN.md)",
-        "config": config_dict(inst, "fp64"),
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (split bf16 tensor-core products)",
+        "data": "synthetic (seeded; see DESIGN.md)",
+        "config": dict(config_dict(inst, args.precision), slices=args.slices if args.precision == "split" else None),
         "effective_tflops_ladder_build": eff_tflops,
         "energies": energies,
+        "comparison": {"precision": other, "ms_per_step": statistics.median(ms2), "value": 1000.0 / statistics.median(ms2),
+                       "energies": e_other, "headline_minus_comparison_Eh": err},
         "clocks": clocks,
         "gpu_launches": launches,
         "roofline": roofline,
-        "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items()},
+        "roofline_tensor": roof_tensor,
+        "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items() if v["launches"]},
         "e2e": {"value": e2e_value, "unit": "energies/s", "h2d_bytes_per_step": input_bytes(inst),
                 "d2h_bytes_per_step": d2h},
     }
@@ -312,7 +348,6 @@ def run_ours(args, rank, world, local_rank):
                                 "sample": text}
     elif rank == 0:
         line["cpu_baseline"] = None
-    h.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -327,6 +362,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-reps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=("split", "fp64"), default="split",
+                    help="headline path; the other is timed alongside for comparison")
+    ap.add_argument("--slices", type=int, default=6)
     args = ap.parse_args(argv)
     rank, world, local_rank = rank_env()
     if args.impl == "reference":

@@ -42,6 +42,9 @@ extern "C" {
                              copied at load as well                            */
 
 #define DSRG_PREC_FP64 0  /* every contraction in FP64                          */
+#define DSRG_PREC_SPLIT 1 /* large contractions as split-precision tensor-core
+                             products (see dsrg_split_gemm); everything else,
+                             the regulariser and all reductions stay FP64     */
 
 typedef struct dsrg_handle dsrg_handle;
 
@@ -79,8 +82,10 @@ typedef struct {
 } dsrg_inputs;
 
 typedef struct {
-  int precision;  /* DSRG_PREC_FP64 */
+  int precision;  /* DSRG_PREC_FP64 or DSRG_PREC_SPLIT                       */
   void *stream;   /* cudaStream_t to run on; NULL = the library's own stream */
+  int slices;     /* DSRG_PREC_SPLIT: 7-bit digit slices per operand (1..7);
+                     0 selects 6                                             */
 } dsrg_options;
 
 typedef struct {

@@ -22,6 +22,7 @@ LIBPATH = os.path.join(HERE, "libdsrg.so")
 DSRG_MEM_HOST = 0
 DSRG_MEM_DEVICE = 1
 DSRG_PREC_FP64 = 0
+DSRG_PREC_SPLIT = 1
 
 _P = ctypes.POINTER(ctypes.c_double)
 
@@ -34,7 +35,7 @@ class dsrg_inputs(ctypes.Structure):
 
 
 class dsrg_options(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+    _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("slices", ctypes.c_int)]
 
 
 class dsrg_energies(ctypes.Structure):
@@ -143,10 +144,10 @@ def make_inputs(inst: dict):
     return s, keep
 
 
-def dsrg_init(inst: dict, stream=None, precision=DSRG_PREC_FP64) -> ctypes.c_void_p:
+def dsrg_init(inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0) -> ctypes.c_void_p:
     L = load_library()
     s, keep = make_inputs(inst)
-    opt = dsrg_options(precision, ctypes.c_void_p(stream) if stream else None)
+    opt = dsrg_options(precision, ctypes.c_void_p(stream) if stream else None, int(slices))
     h = ctypes.c_void_p()
     _check(L.dsrg_init(ctypes.byref(s), ctypes.byref(opt), ctypes.byref(h)))
     return h
@@ -266,9 +267,9 @@ def dsrg_split_gemm(A, B, C, alpha: float = 1.0, slices: int = 6, stream=None) -
 class Dsrg:
     """Convenience owner of one handle."""
 
-    def __init__(self, inst: dict, stream=None):
+    def __init__(self, inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0):
         self.sizes = (int(inst["nc"]), int(inst["na"]), int(inst["nv"]))
-        self.h = dsrg_init(inst, stream)
+        self.h = dsrg_init(inst, stream, precision, slices)
 
     def load(self, inst):
         dsrg_load(self.h, inst)

@@ -7,6 +7,7 @@
 
 #include "../../include/dsrg.h"
 #include "dsrg_impl.cuh"
+#include "ozaki.cuh"
 
 struct dsrg_handle {
   dsrg::Handle* h;
@@ -134,7 +135,13 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
   *out = nullptr;
   int rc = validate(in);
   if (rc) return rc;
-  if (opts && opts->precision != DSRG_PREC_FP64) return fail(DSRG_ERR_ARG, "unsupported precision");
+  if (opts && opts->precision != DSRG_PREC_FP64 && opts->precision != DSRG_PREC_SPLIT)
+    return fail(DSRG_ERR_ARG, "unsupported precision");
+  int slices = 0;
+  if (opts && opts->precision == DSRG_PREC_SPLIT) {
+    slices = opts->slices ? opts->slices : 6;
+    if (slices < 1 || slices > 7) return fail(DSRG_ERR_ARG, "slices must be 1..7");
+  }
   cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
   bool own = false;
   if (!st) {
@@ -148,6 +155,7 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
     return fail(DSRG_ERR_OOM, "host allocation failed");
   }
   h->own_stream = own;
+  h->ws.slices = slices;
   try {
     h->nc = in->nc;
     h->na = in->na;
@@ -212,8 +220,16 @@ static int run(dsrg_handle* hd, bool pt3, dsrg_energies* out) {
   if (!out) return fail(DSRG_ERR_ARG, "out is NULL");
   try {
     double e2 = 0, e3a = 0, e3b = 0;
+    if (hd->h->ws.slices > 0) {
+      int zero = 0;
+      dsrg::check_cuda(cudaMemcpyToSymbolAsync(dsrg::g_oz_status_alias(), &zero, sizeof(int), 0,
+                                               cudaMemcpyHostToDevice, hd->h->stream),
+                       "status reset");
+    }
     dsrg::run_energy(*hd->h, pt3, &e2, &e3a, &e3b);
     dsrg::check_cuda(cudaGetLastError(), "kernel launch");
+    if (hd->h->ws.slices > 0 && dsrg::ozaki_status(hd->h->stream))
+      return fail(DSRG_ERR_CUDA, "a bounded wait in the split-precision kernel ran out");
     dsrg::check_cuda(cudaStreamSynchronize(hd->h->stream), "cudaStreamSynchronize");
     hd->h->ws.prof_collect();
     out->e2 = e2;

@@ -1,0 +1,53 @@
+"""Energies of the split-precision path (large contractions on the tensor
+cores with 6 digit slices) against the oracle and against the FP64 path."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dsrg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_02011_gb300 import build
+    build.build()
+    import paper_1701_02011_gb300 as g
+    g.load_library()
+    return g
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 4, 21, 50), (2, 2, 2, 40, 70)], ids=str)
+def test_split_energies_match_oracle(lib, shape):
+    nc, na, nel, nv, naux = shape
+    inst = synth.make_instance(nc, na, nel, nv, naux, 0.5, seed=sum(shape) + 3)
+    ref = dsrg.dsrg_pt3(inst)
+    h = lib.Dsrg(inst, precision=lib.DSRG_PREC_SPLIT, slices=6)
+    try:
+        e = h.pt3()
+    finally:
+        h.close()
+    for k in ("e2", "e3a", "e3b", "e3"):
+        assert abs(e[k] - ref[k]) < 1e-9, (k, e[k], ref[k])
+
+
+def test_split_matches_fp64_at_the_bench_workload(lib):
+    """CAS(6,6), 10 core, 100 virtual, 400 aux: every component within 1 uEh."""
+    inst = synth.config_instance("cas66_c10_v100_q400")
+    a = lib.Dsrg(inst)
+    b = lib.Dsrg(inst, precision=lib.DSRG_PREC_SPLIT, slices=6)
+    try:
+        e64 = a.pt3()
+        es = b.pt3()
+        st = b.profile_stats()
+    finally:
+        a.close()
+        b.close()
+    for k in ("e2", "e3a", "e3b", "e3"):
+        assert abs(es[k] - e64[k]) < 1e-6, (k, es[k], e64[k])
+    # energies are O(1e3) Eh here: 1e-6 Eh is ~4e-10 relative
+    assert abs(e64["e3"]) > 100.0
