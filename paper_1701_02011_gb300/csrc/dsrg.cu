@@ -236,8 +236,41 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
 // ---------------------------------------------------------------------------
 // [X, T] into one output block pair (C1, C2)
 // ---------------------------------------------------------------------------
+// One-body operator c_f f1 + c_w (W1 + W1^+) as pieces: f1 on [G,G] and W1's
+// excitation block [P,H] with its transpose on [H,P].
+struct Op1Pieces {
+  int n = 0;
+  View v[3];
+  double c[3];
+};
+
+static Op1Pieces op1_pieces(Handle& h, double c_f, const Tensor* W1, double c_w) {
+  Op1Pieces o;
+  if (c_f != 0.0 && h.has_f1) {
+    o.v[o.n] = h.F1.v;
+    o.c[o.n++] = c_f;
+  }
+  if (W1 && c_w != 0.0) {
+    o.v[o.n] = W1->v;
+    o.c[o.n++] = c_w;
+    View t;
+    t.rank = 2;
+    t.p = W1->v.p;
+    t.iv[0] = W1->v.iv[1];
+    t.iv[1] = W1->v.iv[0];
+    t.st[0] = W1->v.st[1];
+    t.st[1] = W1->v.st[0];
+    t.ss[0] = W1->v.ss[1];
+    t.ss[1] = W1->v.ss[0];
+    t.mask = W1->v.mask;  // spin-diagonal: symmetric under the swap
+    o.v[o.n] = t;
+    o.c[o.n++] = c_w;
+  }
+  return o;
+}
+
 void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
-                Tensor& C2, bool df) {
+                Tensor& C2, bool df, const Op1Pieces* X1p) {
   Workspace& ws = h.ws;
   const Tensor& g = h.gam;
   const Tensor& e = h.eta;
@@ -261,11 +294,21 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     contract(ws, -1.0, e.v, "ip", t2.v, "pa", M1, "ia");
     contract(ws, 1.0, M1.v, "ia", T2.v, "abij", C1, "bj");
   }
-  // [X1, T2] two-body
-  contract(ws, 1.0, X1.v, "xa", T2.v, "ayij", C2, "xyij");
-  contract(ws, -1.0, X1.v, "ya", T2.v, "axij", C2, "xyij");
-  contract(ws, -1.0, T2.v, "xyik", X1.v, "kj", C2, "xyij");
-  contract(ws, 1.0, T2.v, "xyjk", X1.v, "ki", C2, "xyij");
+  // [X1, T2] two-body, piece by piece so that only non-zero blocks of X1 enter
+  {
+    Op1Pieces whole;
+    whole.n = 1;
+    whole.v[0] = X1.v;
+    whole.c[0] = 1.0;
+    const Op1Pieces& pc = X1p ? *X1p : whole;
+    for (int k = 0; k < pc.n; ++k) {
+      const double c = pc.c[k];
+      contract(ws, c, pc.v[k], "xa", T2.v, "ayij", C2, "xyij");
+      contract(ws, -c, pc.v[k], "ya", T2.v, "axij", C2, "xyij");
+      contract(ws, -c, T2.v, "xyik", pc.v[k], "kj", C2, "xyij");
+      contract(ws, c, T2.v, "xyjk", pc.v[k], "ki", C2, "xyij");
+    }
+  }
   // [X2, T1] one-body: X2[p,q,s,r] (gamma T1^T eta)[q,r]
   {
     Tensor tmp = mk(h, {H, P});
@@ -401,11 +444,11 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
 
 // excitation blocks of [X, T - T^+] = [X, T] + [X, T]^+ (X Hermitian)
 void commutator_A(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
-                  Tensor& O2, bool df) {
+                  Tensor& O2, bool df, const Op1Pieces* X1p) {
   Tensor C1e = mk(h, {h.P, h.H}), C1d = mk(h, {h.H, h.P});
   Tensor C2e = mk(h, {h.P, h.P, h.H, h.H}), C2d = mk(h, {h.H, h.H, h.P, h.P});
-  commutator(h, X1, X2, T1, T2, C1e, C2e, df);
-  commutator(h, X1, X2, T1, T2, C1d, C2d, df);
+  commutator(h, X1, X2, T1, T2, C1e, C2e, df, X1p);
+  commutator(h, X1, X2, T1, T2, C1d, C2d, df, X1p);
   O1 = mk(h, {h.P, h.H});
   O2 = mk(h, {h.P, h.P, h.H, h.H});
   axpy(h.ws, 1.0, C1e.v, "ai", O1, "ai");
@@ -559,7 +602,8 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   Tensor O1, O2;
   {
     Tensor X1 = build_x1(h, 1.0, &W1, 0.5);
-    commutator_A(h, X1, Op2{&V, 1.0, &W2, 0.5}, t1, t2, O1, O2, true);
+    Op1Pieces pc = op1_pieces(h, 1.0, &W1, 0.5);
+    commutator_A(h, X1, Op2{&V, 1.0, &W2, 0.5}, t1, t2, O1, O2, true, &pc);
   }
   // second-order amplitudes (Eqs. T1_2nd, T2_2nd) and [H(0), A(2)]
   Tensor U1, U2, V1, V2;
@@ -568,7 +612,8 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   Tensor Q1, Q2;
   {
     Tensor Y1 = build_x1(h, 0.0, &W1, 1.0);
-    commutator_A(h, Y1, Op2{nullptr, 0.0, &W2, 1.0}, t1, t2, Q1, Q2, false);
+    Op1Pieces pc = op1_pieces(h, 0.0, &W1, 1.0);
+    commutator_A(h, Y1, Op2{nullptr, 0.0, &W2, 1.0}, t1, t2, Q1, Q2, false, &pc);
   }
   // Htilde(2)_{1,2} excitation blocks = [H0, A(2)] + O - [W, A(1)] / 6
   Tensor Z1 = mk(h, {P, H}), Z2 = mk(h, {P, P, H, H});

@@ -43,10 +43,11 @@ void build_v(Handle& h, unsigned classes, Sym2& V);
 Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M);
 void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tensor& T2, Tensor& W1, Tensor& W2);
 void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef);
+struct Op1Pieces;
 void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
-                Tensor& C2, bool df);
+                Tensor& C2, bool df, const Op1Pieces* X1p);
 void commutator_A(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
-                  Tensor& O2, bool df);
+                  Tensor& O2, bool df, const Op1Pieces* X1p);
 void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2);
 void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b);
 

@@ -102,7 +102,11 @@ void Workspace::prof_collect() {
 
 void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
   if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0 || g0.nbatch <= 0) return;
-  if (ws.slices > 0 && g0.nbatch == 1 && g0.M >= 128 && g0.N >= 128 && g0.K >= 64) {
+  // split-precision tensor-core path for contractions large enough to pay for
+  // the operand slicing (both orientations, narrow tiles down to 32 columns)
+  const long long big = g0.M > g0.N ? g0.M : g0.N, small_side = g0.M > g0.N ? g0.N : g0.M;
+  if (ws.slices > 0 && g0.nbatch == 1 && big >= 128 && small_side >= 16 && g0.K >= 32 &&
+      2.0 * (double)g0.M * (double)g0.N * (double)g0.K >= 4e8) {
     ozaki_gemm(ws, g0, ws.slices, kind == K_GEMM ? (int)K_OZAKI_MMA : kind);
     return;
   }

@@ -9,11 +9,10 @@
 namespace dsrg {
 namespace {
 
-constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64;
+constexpr int OZ_BM = 128, OZ_BK = 64;
 constexpr int OZ_THREADS = 128;
-constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // 8192 bf16 = 16 KiB (A and B tiles alike)
+constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // A tile: 8192 bf16 = 16 KiB
 constexpr int OZ_TILE_BYTES = OZ_TILE_ELEMS * 2;
-constexpr uint32_t OZ_TMEM_COLS = 512;        // acc [0,128) hi [128,256) lo [256,384)
 constexpr long long OZ_WAIT_LIMIT = 1LL << 22;
 
 __device__ int g_oz_status;
@@ -33,9 +32,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 128, M = 128.
-constexpr uint32_t OZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
-                              ((uint32_t)(OZ_BM >> 4) << 24);
+// K-major, M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t oz_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -61,11 +62,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(OZ_IDESC), "r"(acc)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -115,6 +117,10 @@ struct OzArgs {
   int eM[4], eN[4];
   long long cM[4], cN[4];
   int* status;
+  // split over k tiles: CTA z covers [z*ktper, (z+1)*ktper) and writes its
+  // scaled partial tile to part[z][MT*128][NT*BN] instead of C
+  int splits, ktper;
+  double* part;
 };
 
 __device__ __forceinline__ long long c_offset(long long lin, int nd, const int* ext, const long long* st) {
@@ -127,22 +133,29 @@ __device__ __forceinline__ long long c_offset(long long lin, int nd, const int* 
   return o;
 }
 
-// One CTA: a 128 x 128 tile of C.  Thread t owns TMEM lane t (tile row t).
+// One CTA: a 128 x BN tile of C.  Thread t owns TMEM lane t (tile row t).
+// TMEM columns: level accumulator [0,BN), running hi [BN,2BN), lo [2BN,3BN).
+template <int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
+  constexpr uint32_t TMEM_COLS = BN == 128 ? 512 : BN == 64 ? 256 : 128;
+  constexpr int B_TILE_BYTES = BN * OZ_BK * 2;
+  constexpr uint32_t IDESC = oz_idesc<BN>();
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
   unsigned char* sB = smem + (size_t)a.S * OZ_TILE_BYTES;
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
-  __shared__ long long colC[OZ_BN];
-  __shared__ int colE[OZ_BN];
+  __shared__ long long colC[BN];
+  __shared__ int colE[BN];
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int mt = blockIdx.x, nt = blockIdx.y;
+  const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
+  const int kt0 = a.splits > 1 ? z * a.ktper : 0;
+  const int kt1 = a.splits > 1 ? (kt0 + a.ktper < a.KT ? kt0 + a.ktper : a.KT) : a.KT;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(OZ_TMEM_COLS)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -150,10 +163,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int t = tid; t < OZ_BN; t += OZ_THREADS) {
-    long long n = (long long)nt * OZ_BN + t;
+  for (int t = tid; t < BN; t += OZ_THREADS) {
+    long long n = (long long)nt * BN + t;
     colC[t] = n < a.N ? c_offset(n, a.nN, a.eN, a.cN) : -1;
-    colE[t] = a.fb[(long long)nt * OZ_BN + t];
+    colE[t] = a.fb[(long long)nt * BN + t];
   }
   tc_fence_before();
   __syncthreads();
@@ -163,27 +176,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
 
   // zero the running float-float sums (hi, lo)
   {
-    uint32_t z[32];
+    uint32_t zr[32];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) z[q] = 0u;
+    for (int q = 0; q < 32; ++q) zr[q] = 0u;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) tmem_st32(tm + lane_off + 128 + 32 * j, z);
+    for (int j = 0; j < 2 * BN / 32; ++j) tmem_st32(tm + lane_off + BN + 32 * j, zr);
     tmem_wait_st();
   }
   uint32_t phase = 0;
   bool ok = true;
   const int S = a.S;
-  for (int kt = 0; kt < a.KT && ok; ++kt) {
+  for (int kt = kt0; kt < kt1 && ok; ++kt) {
     // stage the S digit tiles of A and of B for this k chunk
     for (int s = 0; s < S; ++s) {
       const uint4* gA = (const uint4*)(a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS);
-      const uint4* gB = (const uint4*)(a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * OZ_TILE_ELEMS);
+      const uint4* gB = (const uint4*)(a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * (BN * OZ_BK));
       uint4* dA = (uint4*)(sA + (size_t)s * OZ_TILE_BYTES);
-      uint4* dB = (uint4*)(sB + (size_t)s * OZ_TILE_BYTES);
-      for (int i = tid; i < OZ_TILE_BYTES / 16; i += OZ_THREADS) {
-        dA[i] = gA[i];
-        dB[i] = gB[i];
-      }
+      uint4* dB = (uint4*)(sB + (size_t)s * B_TILE_BYTES);
+      for (int i = tid; i < OZ_TILE_BYTES / 16; i += OZ_THREADS) dA[i] = gA[i];
+      for (int i = tid; i < B_TILE_BYTES / 16; i += OZ_THREADS) dB[i] = gB[i];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -196,10 +207,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
         for (int t = t0; t <= t1; ++t) {
           const int u = c - t;
           const uint32_t aA = smem_u32(sA + (size_t)(t - 1) * OZ_TILE_BYTES);
-          const uint32_t aB = smem_u32(sB + (size_t)(u - 1) * OZ_TILE_BYTES);
+          const uint32_t aB = smem_u32(sB + (size_t)(u - 1) * B_TILE_BYTES);
 #pragma unroll
           for (int ks = 0; ks < OZ_BK / 16; ++ks) {
-            mma_bf16(tm, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), accum);
+            mma_bf16(tm, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), IDESC, accum);
             accum = 1;
           }
         }
@@ -213,11 +224,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
       // fold level c: (hi, lo) += acc * 2^(-7c), two-sum in FP32
       const float scale = exp2f(-7.0f * (float)c);
 #pragma unroll 1
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < BN / 32; ++j) {
         uint32_t acc[32], hi[32], lo[32];
         tmem_ld32(tm + lane_off + 32 * j, acc);
-        tmem_ld32(tm + lane_off + 128 + 32 * j, hi);
-        tmem_ld32(tm + lane_off + 256 + 32 * j, lo);
+        tmem_ld32(tm + lane_off + BN + 32 * j, hi);
+        tmem_ld32(tm + lane_off + 2 * BN + 32 * j, lo);
         tmem_wait_ld();
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -232,8 +243,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
           hi[q] = __float_as_uint(s2);
           lo[q] = __float_as_uint(l);
         }
-        tmem_st32(tm + lane_off + 128 + 32 * j, hi);
-        tmem_st32(tm + lane_off + 256 + 32 * j, lo);
+        tmem_st32(tm + lane_off + BN + 32 * j, hi);
+        tmem_st32(tm + lane_off + 2 * BN + 32 * j, lo);
       }
       tmem_wait_st();
       tc_fence_before();
@@ -241,18 +252,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
       tc_fence_after();
     }
   }
-  // epilogue: C[m, n] += alpha * 2^(ea[m] + fb[n]) * (hi + lo)
+  // epilogue: alpha * 2^(ea[m] + fb[n]) * (hi + lo) into C, or the scaled
+  // partial into part[z] when K is split
   if (ok) {
     const long long m = (long long)mt * OZ_BM + tid;
     const long long offm = m < a.M ? c_offset(m, a.nM, a.eM, a.cM) : -1;
     const int em = a.ea[(long long)mt * OZ_BM + tid];
+    const long long ldp = (long long)a.NT * BN;
+    double* prow = a.splits > 1 ? a.part + ((long long)z * a.MT * OZ_BM + m) * ldp + (long long)nt * BN : nullptr;
 #pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < BN / 32; ++j) {
       uint32_t hi[32], lo[32];
-      tmem_ld32(tm + lane_off + 128 + 32 * j, hi);
-      tmem_ld32(tm + lane_off + 256 + 32 * j, lo);
+      tmem_ld32(tm + lane_off + BN + 32 * j, hi);
+      tmem_ld32(tm + lane_off + 2 * BN + 32 * j, lo);
       tmem_wait_ld();
-      if (offm >= 0) {
+      if (prow) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          double v = (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]);
+          prow[32 * j + q] = colC[32 * j + q] >= 0 && offm >= 0 ? ldexp(v, em + colE[32 * j + q]) : 0.0;
+        }
+      } else if (offm >= 0) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
           const long long oc = colC[32 * j + q];
@@ -265,9 +285,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(OZ_TMEM_COLS)
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(TMEM_COLS)
                               : "memory");
   if (!ok && tid == 0) atomicExch(a.status ? a.status : &g_oz_status, 1);
+}
+
+// C[m, n] += alpha * sum_z part[z][m][n] (z in order)
+template <int BN>
+__global__ void k_ozaki_reduce(const OzArgs a) {
+  const long long Mp = (long long)a.MT * OZ_BM, ldp = (long long)a.NT * BN;
+  const long long total = a.M * a.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long m = i / a.N, n = i - m * a.N;
+    double s = 0.0;
+    for (int z = 0; z < a.splits; ++z) s += a.part[((long long)z * Mp + m) * ldp + n];
+    a.C[c_offset(m, a.nM, a.eM, a.cM) + c_offset(n, a.nN, a.eN, a.cN)] += a.alpha * s;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -278,50 +312,70 @@ struct OzPack {
   int nR, nK;
   int eR[4], eK[4];
   long long sR[4], sK[4];
-  long long R, K;      // logical sizes
-  int T, KT;           // tiles along rows (128 each) and k (64 each)
+  long long R, K;      // logical sizes (both < 2^31)
+  int T, KT;           // tiles along rows (TR each) and k (64 each)
+  int TR;              // rows per tile: 128 (A) or BN (B)
   int S;
 };
 
-__device__ __forceinline__ long long src_offset(long long lin, int nd, const int* ext, const long long* st) {
+__device__ __forceinline__ long long src_offset32(int lin, int nd, const int* ext, const long long* st) {
   long long o = 0;
   for (int d = nd - 1; d >= 0; --d) {
-    long long q = lin / ext[d];
-    o += (lin - q * ext[d]) * st[d];
+    int q = lin / ext[d];
+    o += (long long)(lin - q * ext[d]) * st[d];
     lin = q;
   }
   return o;
 }
 
-// e[r] = max over k of the binary exponent ex with |x| < 2^ex (frexp)
-__global__ void k_ozaki_exp(const OzPack p, int* e) {
-  const long long total = p.R * p.K;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / p.K, k = i - r * p.K;
-    const double x = p.src[src_offset(r, p.nR, p.eR, p.sR) + src_offset(k, p.nK, p.eK, p.sK)];
-    if (x == 0.0) continue;
-    const long long bits = __double_as_longlong(x);
-    const int be = (int)((bits >> 52) & 0x7FF);
-    atomicMax(&e[r], be ? be - 1022 : -1022);
+// One CTA per row r (rows beyond R and rows of padding write zeros):
+// e[r] = max over k of the binary exponent ex with |x| < 2^ex (frexp), then
+// the S digits of every element of the row go to their swizzled tile slots.
+constexpr int PACK_T = 256;
+
+__device__ __forceinline__ int exp_of(double x) {
+  if (x == 0.0) return -2000;
+  const long long bits = __double_as_longlong(x);
+  const int be = (int)((bits >> 52) & 0x7FF);
+  return be ? be - 1022 : -1022;
+}
+
+__global__ void __launch_bounds__(PACK_T) k_ozaki_pack(const OzPack p, int* e_out, __nv_bfloat16* dst) {
+  const int r = blockIdx.x;  // over T * TR rows (padded)
+  const long long Kp = (long long)p.KT * OZ_BK;
+  const bool live = r < p.R;
+  const long long roff = live ? src_offset32(r, p.nR, p.eR, p.sR) : 0;
+  // row maximum exponent
+  int emax = -2000;
+  if (live)
+    for (int k = threadIdx.x; k < p.K; k += PACK_T) {
+      const int ex = exp_of(p.src[roff + src_offset32(k, p.nK, p.eK, p.sK)]);
+      emax = ex > emax ? ex : emax;
+    }
+  __shared__ int sh[PACK_T / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const int v = __shfl_xor_sync(0xffffffffu, emax, o);
+    emax = v > emax ? v : emax;
   }
-}
-
-__global__ void k_ozaki_fill_int(int* p, long long n, int v) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    p[i] = v;
-}
-
-// digits of every element (zero padding outside the logical matrix)
-__global__ void k_ozaki_pack(const OzPack p, const int* e, __nv_bfloat16* dst) {
-  const long long Rp = (long long)p.T * OZ_BM, Kp = (long long)p.KT * OZ_BK;
-  const long long total = Rp * Kp;
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = emax;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < PACK_T / 32 ? sh[threadIdx.x] : -2000;
+    for (int o = 16; o > 0; o >>= 1) {
+      const int w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+    if (threadIdx.x == 0) sh[0] = v;
+  }
+  __syncthreads();
+  const int e = sh[0];
+  if (threadIdx.x == 0) e_out[r] = e;
   const int F = 7 * p.S;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / Kp, k = i - r * Kp;
+  const long long tile_elems = (long long)p.TR * OZ_BK;
+  const int tr = r / p.TR, rr = r - tr * p.TR;
+  for (long long k = threadIdx.x; k < Kp; k += PACK_T) {
     double x = 0.0;
-    if (r < p.R && k < p.K) x = p.src[src_offset(r, p.nR, p.eR, p.sR) + src_offset(k, p.nK, p.eK, p.sK)];
+    if (live && k < p.K) x = p.src[roff + src_offset32((int)k, p.nK, p.eK, p.sK)];
     unsigned long long v = 0;
     bool neg = false;
     if (x != 0.0) {
@@ -336,18 +390,18 @@ __global__ void k_ozaki_pack(const OzPack p, const int* e, __nv_bfloat16* dst) {
       } else {
         E = -1074;
       }
-      const int sh = E + F - e[r];  // v = m 2^sh < 2^F
-      if (sh >= 0) v = sh < 12 ? (m << sh) : 0;
-      else v = (-sh) >= 64 ? 0 : (m >> (-sh));
+      const int sh_ = E + F - e;  // v = m 2^sh < 2^F
+      if (sh_ >= 0) v = sh_ < 12 ? (m << sh_) : 0;
+      else v = (-sh_) >= 64 ? 0 : (m >> (-sh_));
     }
-    const int tr = (int)(r / OZ_BM), rr = (int)(r % OZ_BM), tk = (int)(k / OZ_BK), kk = (int)(k % OZ_BK);
+    const int tk = (int)(k / OZ_BK), kk = (int)(k - (long long)tk * OZ_BK);
     const int chunk = kk >> 3, j = kk & 7;
     const long long within = (long long)rr * OZ_BK + ((chunk ^ (rr & 7)) << 3) + j;
     for (int t = 1; t <= p.S; ++t) {
       int d = (int)((v >> (7 * (p.S - t))) & 127ULL);
       if (neg) d = -d;
       const long long tile = ((long long)(t - 1) * p.T + tr) * p.KT + tk;
-      dst[tile * OZ_TILE_ELEMS + within] = __float2bfloat16_rn((float)d);
+      dst[tile * tile_elems + within] = __float2bfloat16_rn((float)d);
     }
   }
 }
@@ -365,16 +419,23 @@ int* oz_status_ptr() {
   return p;
 }
 
-size_t oz_smem_bytes(int S) { return (size_t)2 * S * OZ_TILE_BYTES + 1024; }
+size_t oz_smem_bytes(int S, int BN) { return (size_t)S * OZ_TILE_BYTES + (size_t)S * BN * OZ_BK * 2 + 1024; }
 
-void oz_launch_mma(const OzArgs& a, int MT, int NT, cudaStream_t st) {
-  // at least 120 KiB so that one CTA (and one 512-column TMEM allocation)
-  // occupies an SM
-  size_t smem = oz_smem_bytes(a.S);
+template <int BN>
+void oz_launch_bn(const OzArgs& a, int MT, int NT, cudaStream_t st) {
+  // at least 120 KiB so that one CTA (one TMEM allocation) occupies an SM
+  size_t smem = oz_smem_bytes(a.S, BN);
   if (smem < 120 * 1024) smem = 120 * 1024;
-  check_cuda(cudaFuncSetAttribute(k_ozaki_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  check_cuda(cudaFuncSetAttribute(k_ozaki_mma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
              "cudaFuncSetAttribute (ozaki)");
-  k_ozaki_mma<<<dim3(MT, NT), OZ_THREADS, smem, st>>>(a);
+  k_ozaki_mma<BN><<<dim3(MT, NT, a.splits > 1 ? a.splits : 1), OZ_THREADS, smem, st>>>(a);
+  if (a.splits > 1) k_ozaki_reduce<BN><<<oz_grid(a.M * a.N), 256, 0, st>>>(a);
+}
+
+void oz_launch_mma(const OzArgs& a, int MT, int NT, int BN, cudaStream_t st) {
+  if (BN == 32) oz_launch_bn<32>(a, MT, NT, st);
+  else if (BN == 64) oz_launch_bn<64>(a, MT, NT, st);
+  else oz_launch_bn<128>(a, MT, NT, st);
 }
 }  // namespace
 
@@ -387,86 +448,99 @@ int ozaki_status(cudaStream_t st) {
   return v;
 }
 
-void ozaki_mma_raw(const void* As, const void* Bs, const int* ea, const int* fb, int S, long long M, long long N,
-                   int MT, int NT, int KT, double alpha, double* C, long long ldc, int* status, cudaStream_t st) {
-  OzArgs a{};
-  a.As = (const __nv_bfloat16*)As;
-  a.Bs = (const __nv_bfloat16*)Bs;
-  a.ea = ea;
-  a.fb = fb;
-  a.S = S;
-  a.MT = MT;
-  a.NT = NT;
-  a.KT = KT;
-  a.M = M;
-  a.N = N;
-  a.alpha = alpha;
-  a.C = C;
-  a.nM = 1;
-  a.eM[0] = (int)M;
-  a.cM[0] = ldc;
-  a.nN = 1;
-  a.eN[0] = (int)N;
-  a.cN[0] = 1;
-  a.status = status;
-  oz_launch_mma(a, MT, NT, st);
-}
-
-void ozaki_gemm(Workspace& ws, const GemmArgs& g, int S, int kind) {
-  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return;
-  if (g.nbatch != 1) throw std::runtime_error("split-precision contraction needs nbatch == 1");
+void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
+  if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0) return;
+  if (g0.nbatch != 1) throw std::runtime_error("split-precision contraction needs nbatch == 1");
   if (S < 1 || S > kOzakiMaxSlices) throw std::runtime_error("split-precision slices must be 1..7");
-  const int MT = (int)((g.M + OZ_BM - 1) / OZ_BM), NT = (int)((g.N + OZ_BN - 1) / OZ_BN);
-  const int KT = (int)((g.K + OZ_BK - 1) / OZ_BK);
+  if (g0.M >= (1LL << 31) || g0.N >= (1LL << 31) || g0.K >= (1LL << 31))
+    throw std::runtime_error("split-precision contraction sizes must stay below 2^31");
+  // orient so that the longer output side runs along the 128-row A tiles:
+  // C^T = B^T A^T just exchanges the roles of the operands
+  const bool swap = g0.N > g0.M;
+  OzPack pa{}, pb{};
+  OzArgs a{};
+  auto fill = [&](OzPack& p, const double* src, int nR, const int* eR, const long long* sR) {
+    p.src = src;
+    p.nR = nR;
+    p.nK = g0.nK;
+    for (int d = 0; d < 4; ++d) {
+      p.eR[d] = eR[d];
+      p.sR[d] = sR[d];
+      p.eK[d] = g0.eK[d];
+    }
+    p.K = g0.K;
+    p.S = S;
+  };
+  long long M, N;
+  if (!swap) {
+    fill(pa, g0.A, g0.nM, g0.eM, g0.aM);
+    for (int d = 0; d < 4; ++d) pa.sK[d] = g0.aK[d];
+    fill(pb, g0.B, g0.nN, g0.eN, g0.bN);
+    for (int d = 0; d < 4; ++d) pb.sK[d] = g0.bK[d];
+    M = g0.M;
+    N = g0.N;
+    a.nM = g0.nM;
+    a.nN = g0.nN;
+    for (int d = 0; d < 4; ++d) {
+      a.eM[d] = g0.eM[d];
+      a.cM[d] = g0.cM[d];
+      a.eN[d] = g0.eN[d];
+      a.cN[d] = g0.cN[d];
+    }
+  } else {
+    fill(pa, g0.B, g0.nN, g0.eN, g0.bN);
+    for (int d = 0; d < 4; ++d) pa.sK[d] = g0.bK[d];
+    fill(pb, g0.A, g0.nM, g0.eM, g0.aM);
+    for (int d = 0; d < 4; ++d) pb.sK[d] = g0.aK[d];
+    M = g0.N;
+    N = g0.M;
+    a.nM = g0.nN;
+    a.nN = g0.nM;
+    for (int d = 0; d < 4; ++d) {
+      a.eM[d] = g0.eN[d];
+      a.cM[d] = g0.cN[d];
+      a.eN[d] = g0.eM[d];
+      a.cN[d] = g0.cM[d];
+    }
+  }
+  const int BN = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  const int MT = (int)((M + OZ_BM - 1) / OZ_BM), NT = (int)((N + BN - 1) / BN);
+  const int KT = (int)((g0.K + OZ_BK - 1) / OZ_BK);
+  pa.R = M;
+  pa.T = MT;
+  pa.TR = OZ_BM;
+  pa.KT = KT;
+  pb.R = N;
+  pb.T = NT;
+  pb.TR = BN;
+  pb.KT = KT;
+  // spread a short output over more CTAs by splitting the k tiles
+  int splits = 1, ktper = KT;
+  const long long ctas = (long long)MT * NT;
+  if (ctas < 2 * 152 && KT >= 8) {
+    long long sp = (2 * 152 + ctas - 1) / ctas;
+    if (sp > KT / 4) sp = KT / 4;
+    if (sp >= 2) {
+      ktper = (KT + (int)sp - 1) / (int)sp;
+      splits = (KT + ktper - 1) / ktper;
+    }
+  }
   cudaStream_t st = ws.stream;
-  size_t capA, capB, capE;
-  const size_t nA = (size_t)S * MT * KT * OZ_TILE_ELEMS, nB = (size_t)S * NT * KT * OZ_TILE_ELEMS;
-  // bf16 buffers carved from double-sized workspace blocks
-  double* bufA = ws.get((nA + 3) / 4, capA);
+  size_t capA, capB, capE, capP = 0;
+  const size_t nA = (size_t)S * MT * KT * OZ_TILE_ELEMS, nB = (size_t)S * NT * KT * BN * OZ_BK;
+  double* bufA = ws.get((nA + 3) / 4, capA);  // bf16 digit tiles in double-sized blocks
   double* bufB = ws.get((nB + 3) / 4, capB);
-  const size_t nE = (size_t)MT * OZ_BM + (size_t)NT * OZ_BN;
+  const size_t nE = (size_t)MT * OZ_BM + (size_t)NT * BN;
   double* bufE = ws.get((nE + 1) / 2, capE);
+  double* part = nullptr;
+  if (splits > 1) part = ws.get((size_t)splits * MT * OZ_BM * NT * BN, capP);
   int* ea = (int*)bufE;
   int* fb = ea + (size_t)MT * OZ_BM;
-  OzPack pa{};
-  pa.src = g.A;
-  pa.nR = g.nM;
-  pa.nK = g.nK;
-  for (int d = 0; d < 4; ++d) {
-    pa.eR[d] = g.eM[d];
-    pa.sR[d] = g.aM[d];
-    pa.eK[d] = g.eK[d];
-    pa.sK[d] = g.aK[d];
-  }
-  pa.R = g.M;
-  pa.K = g.K;
-  pa.T = MT;
-  pa.KT = KT;
-  pa.S = S;
-  OzPack pb{};
-  pb.src = g.B;
-  pb.nR = g.nN;
-  pb.nK = g.nK;
-  for (int d = 0; d < 4; ++d) {
-    pb.eR[d] = g.eN[d];
-    pb.sR[d] = g.bN[d];
-    pb.eK[d] = g.eK[d];
-    pb.sK[d] = g.bK[d];
-  }
-  pb.R = g.N;
-  pb.K = g.K;
-  pb.T = NT;
-  pb.KT = KT;
-  pb.S = S;
-  int r = ws.begin(K_OZAKI_PACK, 0.0, 8.0 * (double)(g.M + g.N) * (double)g.K * 2.0);
-  k_ozaki_fill_int<<<oz_grid((long long)nE), 256, 0, st>>>(ea, (long long)nE, -2000);
-  k_ozaki_exp<<<oz_grid(g.M * g.K), 256, 0, st>>>(pa, ea);
-  k_ozaki_exp<<<oz_grid(g.N * g.K), 256, 0, st>>>(pb, fb);
-  k_ozaki_pack<<<oz_grid((long long)MT * OZ_BM * KT * OZ_BK), 256, 0, st>>>(pa, ea, (__nv_bfloat16*)bufA);
-  k_ozaki_pack<<<oz_grid((long long)NT * OZ_BN * KT * OZ_BK), 256, 0, st>>>(pb, fb, (__nv_bfloat16*)bufB);
+  int r = ws.begin(K_OZAKI_PACK, 0.0, 8.0 * (double)(M + N) * (double)g0.K * 2.0);
+  k_ozaki_pack<<<(unsigned)(MT * OZ_BM), PACK_T, 0, st>>>(pa, ea, (__nv_bfloat16*)bufA);
+  k_ozaki_pack<<<(unsigned)(NT * BN), PACK_T, 0, st>>>(pb, fb, (__nv_bfloat16*)bufB);
   ws.end(r);
-  ws.launches += 4;
-  OzArgs a{};
+  ws.launches += 1;
   a.As = (const __nv_bfloat16*)bufA;
   a.Bs = (const __nv_bfloat16*)bufB;
   a.ea = ea;
@@ -475,27 +549,24 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g, int S, int kind) {
   a.MT = MT;
   a.NT = NT;
   a.KT = KT;
-  a.M = g.M;
-  a.N = g.N;
-  a.alpha = g.alpha;
-  a.C = g.C;
-  a.nM = g.nM;
-  a.nN = g.nN;
-  for (int d = 0; d < 4; ++d) {
-    a.eM[d] = g.eM[d];
-    a.cM[d] = g.cM[d];
-    a.eN[d] = g.eN[d];
-    a.cN[d] = g.cN[d];
-  }
+  a.M = M;
+  a.N = N;
+  a.alpha = g0.alpha;
+  a.C = g0.C;
   a.status = nullptr;
-  // executed tensor-core flops: pairs with t + u <= S + 1, padded tiles
+  a.splits = splits;
+  a.ktper = ktper;
+  a.part = part;
+  // executed tensor-core flops: digit pairs with t + u <= S + 1, padded tiles
   const double pairs = (double)S * (S + 1) / 2.0;
-  r = ws.begin(kind, 2.0 * pairs * (double)MT * OZ_BM * (double)NT * OZ_BN * (double)KT * OZ_BK, 0.0);
-  oz_launch_mma(a, MT, NT, st);
+  r = ws.begin(kind, 2.0 * pairs * (double)MT * OZ_BM * (double)NT * BN * (double)KT * OZ_BK, 0.0);
+  oz_launch_mma(a, MT, NT, BN, st);
   ws.end(r);
+  if (splits > 1) ws.launches++;
   ws.put(bufA, capA);
   ws.put(bufB, capB);
   ws.put(bufE, capE);
+  if (part) ws.put(part, capP);
 }
 
 }  // namespace dsrg

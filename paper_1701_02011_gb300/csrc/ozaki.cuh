@@ -29,10 +29,4 @@ const void* g_oz_status_alias();
 // (nbatch must be 1) with `slices` digits per operand.  Scratch comes from ws.
 void ozaki_gemm(Workspace& ws, const GemmArgs& g, int slices, int kind);
 
-// Exact test helper: the same kernel on already-sliced inputs.
-//   As: [S][MT][KT][128][64] bf16 tiles (swizzled), Bs: [S][NT][KT][128][64]
-//   ea[Mpad], fb[Npad] power-of-two exponents; C[M][N] row-major (ldc).
-void ozaki_mma_raw(const void* As, const void* Bs, const int* ea, const int* fb, int S, long long M, long long N,
-                   int MT, int NT, int KT, double alpha, double* C, long long ldc, int* status, cudaStream_t st);
-
 }  // namespace dsrg

@@ -46,3 +46,17 @@ def test_many_slices_match_fp64(lib, slices, tol):
     lib.dsrg_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, -0.5, slices)
     err = np.abs(C.cpu().numpy() - (C0 - 0.5 * ref)) / bound
     assert err.max() < tol
+
+
+@pytest.mark.parametrize("M,N,K", [(300, 20, 500), (60, 700, 130), (100, 40, 20000), (129, 129, 65)])
+def test_tile_shapes_orientation_and_k_split(lib, M, N, K):
+    """Narrow N tiles (32/64), the transposed orientation (M < N), a long K
+    split over CTAs, and ragged edges; exact on small integers with one slice."""
+    import torch
+    rng = np.random.default_rng(M + N + K)
+    A = rng.integers(-127, 128, (M, K)).astype(np.float64)
+    B = rng.integers(-127, 128, (K, N)).astype(np.float64)
+    ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
+    C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    lib.dsrg_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 1.0, 1)
+    assert np.array_equal(C.cpu().numpy(), ref)
