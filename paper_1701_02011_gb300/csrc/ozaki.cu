@@ -10,7 +10,7 @@ namespace dsrg {
 namespace {
 
 constexpr int OZ_BM = 128, OZ_BK = 64;
-constexpr int OZ_THREADS = 128;
+constexpr int OZ_THREADS = 256;  // 8 warps: lane quadrant (warp % 4) x column half (warp / 4)
 constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // A tile: 8192 bf16 = 16 KiB
 constexpr int OZ_TILE_BYTES = OZ_TILE_ELEMS * 2;
 constexpr long long OZ_WAIT_LIMIT = 1LL << 22;
@@ -57,6 +57,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
   for (long long i = 0; i < OZ_WAIT_LIMIT; ++i)
     if (mbar_try(bar, phase)) return true;
   return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared bulk copy (bytes a multiple of 16, both addresses 16-byte
+// aligned), completion counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -140,15 +153,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   constexpr uint32_t TMEM_COLS = BN == 128 ? 512 : BN == 64 ? 256 : 128;
   constexpr int B_TILE_BYTES = BN * OZ_BK * 2;
   constexpr uint32_t IDESC = oz_idesc<BN>();
+  // columns per warp in the fold and epilogue: two column halves for BN >= 64;
+  // for BN = 32 the second half of the warps sits out
+  constexpr int HALF = BN >= 64 ? BN / 2 : BN;
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
   unsigned char* sB = smem + (size_t)a.S * OZ_TILE_BYTES;
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar_mma, bar_load;
   __shared__ uint32_t tmem_base;
   __shared__ long long colC[BN];
   __shared__ int colE[BN];
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32*quad.., columns half*HALF..
+  const int row = quad * 32 + (tid & 31);
   const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
   const int kt0 = a.splits > 1 ? z * a.ktper : 0;
   const int kt1 = a.splits > 1 ? (kt0 + a.ktper < a.KT ? kt0 + a.ktper : a.KT) : a.KT;
@@ -160,7 +178,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar_mma, 1);
+    mbar_init(&bar_load, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int t = tid; t < BN; t += OZ_THREADS) {
@@ -172,33 +191,39 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tm = tmem_base;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+  const uint32_t col0 = (uint32_t)(half * HALF);
+  const int nchunk = (BN >= 64 || half == 0) ? HALF / 32 : 0;  // 32-column chunks of this warp
 
-  // zero the running float-float sums (hi, lo)
+  // zero the running float-float sums (hi, lo) of this thread's columns
   {
     uint32_t zr[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) zr[q] = 0u;
 #pragma unroll
-    for (int j = 0; j < 2 * BN / 32; ++j) tmem_st32(tm + lane_off + BN + 32 * j, zr);
+    for (int j = 0; j < nchunk; ++j) {
+      tmem_st32(tm + lane_off + BN + col0 + 32 * j, zr);
+      tmem_st32(tm + lane_off + 2 * BN + col0 + 32 * j, zr);
+    }
     tmem_wait_st();
   }
-  uint32_t phase = 0;
+  uint32_t ph_mma = 0, ph_load = 0;
   bool ok = true;
   const int S = a.S;
   for (int kt = kt0; kt < kt1 && ok; ++kt) {
-    // stage the S digit tiles of A and of B for this k chunk
-    for (int s = 0; s < S; ++s) {
-      const uint4* gA = (const uint4*)(a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS);
-      const uint4* gB = (const uint4*)(a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * (BN * OZ_BK));
-      uint4* dA = (uint4*)(sA + (size_t)s * OZ_TILE_BYTES);
-      uint4* dB = (uint4*)(sB + (size_t)s * B_TILE_BYTES);
-      for (int i = tid; i < OZ_TILE_BYTES / 16; i += OZ_THREADS) dA[i] = gA[i];
-      for (int i = tid; i < B_TILE_BYTES / 16; i += OZ_THREADS) dB[i] = gB[i];
+    // stage the S digit tiles of A and of B for this k chunk (bulk copies)
+    if (tid == 0) {
+      mbar_expect_tx(&bar_load, (uint32_t)(S * (OZ_TILE_BYTES + B_TILE_BYTES)));
+      for (int s = 0; s < S; ++s) {
+        bulk_g2s(sA + (size_t)s * OZ_TILE_BYTES, a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS,
+                 OZ_TILE_BYTES, &bar_load);
+        bulk_g2s(sB + (size_t)s * B_TILE_BYTES, a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * (BN * OZ_BK),
+                 B_TILE_BYTES, &bar_load);
+      }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
+    ok = mbar_wait(&bar_load, ph_load);
+    ph_load ^= 1;
+    ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
     for (int c = 2; c <= S + 1 && ok; ++c) {
       if (tid == 0) {
@@ -214,21 +239,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
             accum = 1;
           }
         }
-        mma_commit(&bar);
+        mma_commit(&bar_mma);
       }
-      ok = mbar_wait(&bar, phase);
-      phase ^= 1;
+      ok = mbar_wait(&bar_mma, ph_mma);
+      ph_mma ^= 1;
       ok = __syncthreads_and(ok) != 0;
       tc_fence_after();
       if (!ok) break;
       // fold level c: (hi, lo) += acc * 2^(-7c), two-sum in FP32
       const float scale = exp2f(-7.0f * (float)c);
 #pragma unroll 1
-      for (int j = 0; j < BN / 32; ++j) {
+      for (int j = 0; j < nchunk; ++j) {
         uint32_t acc[32], hi[32], lo[32];
-        tmem_ld32(tm + lane_off + 32 * j, acc);
-        tmem_ld32(tm + lane_off + BN + 32 * j, hi);
-        tmem_ld32(tm + lane_off + 2 * BN + 32 * j, lo);
+        const uint32_t cc = col0 + 32 * j;
+        tmem_ld32(tm + lane_off + cc, acc);
+        tmem_ld32(tm + lane_off + BN + cc, hi);
+        tmem_ld32(tm + lane_off + 2 * BN + cc, lo);
         tmem_wait_ld();
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -243,8 +269,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
           hi[q] = __float_as_uint(s2);
           lo[q] = __float_as_uint(l);
         }
-        tmem_st32(tm + lane_off + BN + 32 * j, hi);
-        tmem_st32(tm + lane_off + 2 * BN + 32 * j, lo);
+        tmem_st32(tm + lane_off + BN + cc, hi);
+        tmem_st32(tm + lane_off + 2 * BN + cc, lo);
       }
       tmem_wait_st();
       tc_fence_before();
@@ -255,30 +281,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   // epilogue: alpha * 2^(ea[m] + fb[n]) * (hi + lo) into C, or the scaled
   // partial into part[z] when K is split
   if (ok) {
-    const long long m = (long long)mt * OZ_BM + tid;
+    const long long m = (long long)mt * OZ_BM + row;
     const long long offm = m < a.M ? c_offset(m, a.nM, a.eM, a.cM) : -1;
-    const int em = a.ea[(long long)mt * OZ_BM + tid];
+    const int em = a.ea[(long long)mt * OZ_BM + row];
     const long long ldp = (long long)a.NT * BN;
     double* prow = a.splits > 1 ? a.part + ((long long)z * a.MT * OZ_BM + m) * ldp + (long long)nt * BN : nullptr;
 #pragma unroll 1
-    for (int j = 0; j < BN / 32; ++j) {
+    for (int j = 0; j < nchunk; ++j) {
       uint32_t hi[32], lo[32];
-      tmem_ld32(tm + lane_off + BN + 32 * j, hi);
-      tmem_ld32(tm + lane_off + 2 * BN + 32 * j, lo);
+      const int cc = (int)col0 + 32 * j;
+      tmem_ld32(tm + lane_off + BN + cc, hi);
+      tmem_ld32(tm + lane_off + 2 * BN + cc, lo);
       tmem_wait_ld();
       if (prow) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
           double v = (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]);
-          prow[32 * j + q] = colC[32 * j + q] >= 0 && offm >= 0 ? ldexp(v, em + colE[32 * j + q]) : 0.0;
+          prow[cc + q] = colC[cc + q] >= 0 && offm >= 0 ? ldexp(v, em + colE[cc + q]) : 0.0;
         }
       } else if (offm >= 0) {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-          const long long oc = colC[32 * j + q];
+          const long long oc = colC[cc + q];
           if (oc < 0) continue;
           double v = (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]);
-          a.C[offm + oc] += a.alpha * ldexp(v, em + colE[32 * j + q]);
+          a.C[offm + oc] += a.alpha * ldexp(v, em + colE[cc + q]);
         }
       }
     }
