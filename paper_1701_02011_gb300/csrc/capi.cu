@@ -177,7 +177,10 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
     h->ws.cap_results = 1 << 16;
     dsrg::check_cuda(cudaMalloc(&h->ws.results, h->ws.cap_results * sizeof(double)), "cudaMalloc (results)");
     h->ws.dot_scratch_len = 2 * 152 * 16;
-    dsrg::check_cuda(cudaMalloc(&h->ws.dot_scratch, h->ws.dot_scratch_len * sizeof(double)), "cudaMalloc (scratch)");
+    dsrg::check_cuda(cudaMalloc(&h->ws.dot_scratch, (h->ws.dot_scratch_len + 2) * sizeof(double)),
+                     "cudaMalloc (scratch)");
+    h->ws.dot_ticket = reinterpret_cast<unsigned*>(h->ws.dot_scratch + h->ws.dot_scratch_len);
+    dsrg::check_cuda(cudaMemsetAsync(h->ws.dot_ticket, 0, 2 * sizeof(double), st), "cudaMemsetAsync (ticket)");
     load_inputs(*h, in);
     dsrg::check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize (init)");
   } catch (const std::exception& e) {

@@ -83,8 +83,9 @@ void Workspace::prof_collect() {
     std::sort(order.begin(), order.end(), [](auto& x, auto& y) { return x.first > y.first; });
     for (int i = 0; i < (int)order.size() && i < atoi(top); ++i) {
       const Rec& r = recs[order[i].second];
-      fprintf(stderr, "[dsrg] %-10s %9.3f ms  M=%lld N=%lld K=%lld  %.3f TFLOP/s\n", kernel_name(r.id),
-              order[i].first, r.m, r.n, r.k, r.flops / (order[i].first * 1e-3) / 1e12);
+      fprintf(stderr, "[dsrg] %-10s %9.3f ms  M=%lld N=%lld K=%lld  %.3f TFLOP/s %.0f GB/s\n", kernel_name(r.id),
+              order[i].first, r.m, r.n, r.k, r.flops / (order[i].first * 1e-3) / 1e12,
+              r.bytes / (order[i].first * 1e-3) / 1e9);
     }
   }
   for (auto& r : recs) {
@@ -102,12 +103,29 @@ void Workspace::prof_collect() {
 
 void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
   if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0 || g0.nbatch <= 0) return;
-  // split-precision tensor-core path for contractions large enough to pay for
-  // the operand slicing (both orientations, narrow tiles down to 32 columns)
-  const long long big = g0.M > g0.N ? g0.M : g0.N, small_side = g0.M > g0.N ? g0.N : g0.M;
-  if (ws.slices > 0 && g0.nbatch == 1 && big >= 128 && small_side >= 16 && g0.K >= 32 &&
-      2.0 * (double)g0.M * (double)g0.N * (double)g0.K >= 4e8) {
+  // split-precision tensor-core path for every contraction with enough work
+  // to pay for the operand slicing (about 40 us on the FP64 units); narrow
+  // outputs use 32-column tiles, short ones split k over CTAs
+  if (ws.slices > 0 && g0.nbatch == 1 && g0.K >= 32 && 2.0 * (double)g0.M * (double)g0.N * (double)g0.K >= 5e7 &&
+      ozaki_supported(g0)) {
     ozaki_gemm(ws, g0, ws.slices, kind == K_GEMM ? (int)K_OZAKI_MMA : kind);
+    return;
+  }
+  if (kind == K_GEMM && gemm_use_flat(g0)) {
+    const FlatPlan fp = gemm_flat_plan(g0);
+    double* fpart = nullptr;
+    size_t fcap = 0;
+    if (fp.z > 1) fpart = ws.get((size_t)fp.z * (size_t)(g0.M * g0.N * g0.nbatch), fcap);
+    int r = ws.begin(kind, 2.0 * (double)g0.M * (double)g0.N * (double)g0.K * (double)g0.nbatch, 0.0);
+    if (r >= 0) {
+      ws.recs[r].m = g0.M;
+      ws.recs[r].n = g0.N;
+      ws.recs[r].k = g0.K * g0.nbatch;
+    }
+    launch_gemm_flat(g0, fp, fpart, ws.stream);
+    ws.end(r);
+    if (fp.z > 1) ws.launches++;
+    if (fpart) ws.put(fpart, fcap);
     return;
   }
   GemmArgs g = g0;
@@ -162,6 +180,7 @@ void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
   }
   launch_gemm(g, ws.stream, kind == K_LADDER_BUILD ? 1 : kind == K_LADDER_CONTRACT ? 2 : 0);
   ws.end(r);
+  if (g.splits > 1) ws.launches++;  // the split-K reduction
   if (part) ws.put(part, cap);  // stream order keeps later reuse behind the reduction
 }
 
@@ -419,21 +438,34 @@ void axpy(Workspace& ws, double alpha, const View& A, const char* la, Tensor& C,
     if (l.inA < 0 || l.inC < 0) throw std::runtime_error("axpy: label sets differ");
   }
   View a = restrict_view(A, la, L), c = restrict_view(C.v, lc, L);
+  NdArgs g{};
+  g.nd = (int)L.size();
+  g.total = 1;
+  for (int i = 0; i < g.nd; ++i) {
+    g.e[i] = L[i].iv.len();
+    g.sa[i] = a.st[L[i].inA];
+    g.sb[i] = c.st[L[i].inC];
+    g.total *= g.e[i];
+  }
+  // every non-zero spin block of A, one launch (the C blocks are distinct)
+  AxpyBlocks blk{};
+  auto flush = [&]() {
+    if (blk.n == 0) return;
+    int r = ws.begin(K_AXPY, 0.0, 24.0 * (double)g.total * blk.n);
+    launch_axpy_blocks(g, alpha, blk, ws.stream);
+    ws.end(r);
+    blk.n = 0;
+  };
   for (int assign = 0; assign < (1 << L.size()); ++assign) {
     int ba = spin_bits(a, la, L, assign), bc = spin_bits(c, lc, L, assign);
     if (!((a.mask >> ba) & 1)) continue;
-    NdArgs g{};
-    g.nd = (int)L.size();
-    g.total = 1;
-    for (int i = 0; i < g.nd; ++i) {
-      g.e[i] = L[i].iv.len();
-      g.sa[i] = a.st[L[i].inA];
-      g.sb[i] = c.st[L[i].inC];
-      g.total *= g.e[i];
-    }
-    run_axpy(ws, g, alpha, a.p + spin_off(a, ba), c.p + spin_off(c, bc));
+    blk.a[blk.n] = a.p + spin_off(a, ba);
+    blk.c[blk.n] = c.p + spin_off(c, bc);
+    ++blk.n;
     C.v.mask |= 1ULL << bc;
+    if (blk.n == kMaxBlocks) flush();
   }
+  flush();
 }
 
 void dot(Workspace& ws, double alpha, const View& A, const char* la, const View& B, const char* lb) {
@@ -445,26 +477,34 @@ void dot(Workspace& ws, double alpha, const View& A, const char* la, const View&
     if (l.inA < 0 || l.inB < 0) throw std::runtime_error("dot: label sets differ");
   }
   View a = restrict_view(A, la, L), b = restrict_view(B, lb, L);
+  NdArgs g{};
+  g.nd = (int)L.size();
+  g.total = 1;
+  for (int i = 0; i < g.nd; ++i) {
+    g.e[i] = L[i].iv.len();
+    g.sa[i] = a.st[L[i].inA];
+    g.sb[i] = b.st[L[i].inB];
+    g.total *= g.e[i];
+  }
+  // all spin blocks that are non-zero in both operands: one launch, one result slot
+  DotBlocks blk{};
+  auto flush = [&]() {
+    if (blk.n == 0) return;
+    if (ws.nresults >= ws.cap_results) throw std::runtime_error("out of result slots");
+    int r = ws.nresults++;
+    int rec = ws.begin(K_DOT, 2.0 * (double)g.total * blk.n, 16.0 * (double)g.total * blk.n);
+    launch_dot_blocks(g, alpha, blk, ws.dot_scratch, ws.dot_scratch_len, ws.dot_ticket, ws.results + r, ws.stream);
+    ws.end(rec);
+    blk.n = 0;
+  };
   for (int assign = 0; assign < (1 << L.size()); ++assign) {
     int ba = spin_bits(a, la, L, assign), bb = spin_bits(b, lb, L, assign);
     if (!((a.mask >> ba) & 1) || !((b.mask >> bb) & 1)) continue;
-    NdArgs g{};
-    g.nd = (int)L.size();
-    g.total = 1;
-    for (int i = 0; i < g.nd; ++i) {
-      g.e[i] = L[i].iv.len();
-      g.sa[i] = a.st[L[i].inA];
-      g.sb[i] = b.st[L[i].inB];
-      g.total *= g.e[i];
-    }
-    if (ws.nresults >= ws.cap_results) throw std::runtime_error("out of result slots");
-    int r = ws.nresults++;
-    int rec = ws.begin(K_DOT, 2.0 * (double)g.total, 16.0 * (double)g.total);
-    ws.launches++;  // partial + final reduction
-    launch_dot(g, alpha, a.p + spin_off(a, ba), b.p + spin_off(b, bb), ws.dot_scratch, ws.dot_scratch_len,
-               ws.results + r, ws.stream);
-    ws.end(rec);
+    blk.a[blk.n] = a.p + spin_off(a, ba);
+    blk.b[blk.n] = b.p + spin_off(b, bb);
+    if (++blk.n == kMaxBlocks) flush();
   }
+  flush();
 }
 
 // ---------------------------------------------------------------------------

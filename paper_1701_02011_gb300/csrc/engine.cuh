@@ -71,8 +71,9 @@ class Workspace {
   // result slots of scalar reductions (device) and their host copy
   double* results = nullptr;
   int nresults = 0, cap_results = 0;
-  double* dot_scratch = nullptr;
+  double* dot_scratch = nullptr;  // dot_scratch_len doubles, then the ticket of the one-launch dot
   int dot_scratch_len = 0;
+  unsigned* dot_ticket = nullptr;  // zero between launches
   long long launches = 0;
   // > 0: large contractions run as split-precision tensor-core products with
   // this many 7-bit digit slices per operand; 0: FP64 everywhere

@@ -2,6 +2,7 @@
 #include "kernels.cuh"
 
 #include <cmath>
+#include <stdexcept>
 
 namespace dsrg {
 
@@ -13,7 +14,7 @@ namespace dsrg {
 // offA(m) + offA(k), so the tile's row/column/k offsets are decoded once
 // into shared memory and the inner loop is a plain tiled GEMM.
 namespace {
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
 __device__ __forceinline__ void decode(long long lin, int nd, const int* ext, const long long* s1,
                                        const long long* s2, long long& o1, long long& o2) {
@@ -239,6 +240,174 @@ __global__ void __launch_bounds__(TPO_T) k_gemm_tpo(const GemmArgs g, int mfast)
   }
 }
 
+// Flat contraction: one thread per output element and k chunk, 32
+// consecutive outputs per warp along the output index whose operand stride
+// is smallest.  The k multi-index (padded to four dimensions) is decoded once
+// per thread and then stepped like an odometer, so the inner loop is two
+// loads and one FMA with no index division.  WK warps of a CTA take WK
+// consecutive k chunks of the same 32 outputs and are summed in shared memory
+// in a fixed order; gridDim.y > 1 leaves one partial per CTA row in part[z]
+// for k_gemm_flat_reduce.  Nothing is padded, which matters on an SM with two
+// FP64 FMA lanes per clock.
+struct FlatK {
+  int e[4];
+  long long a[4], b[4];    // strides of A and B along the padded k dims
+  long long wa[4], wb[4];  // offset change when dim d wraps into dim d-1
+  FastDiv fk[4];           // divisors of the padded k dims
+  FastDiv fM, fN, fm[4], fn[4], fb[4];
+};
+
+// (m, n, batch) of output o and its operand offsets; every index < 2^31
+__device__ __forceinline__ void flat_out(const GemmArgs& g, const FlatK& fk, long long o, int mfast, long long& oA,
+                                         long long& oB, long long& oC) {
+  unsigned m, n, b;
+  const unsigned uo = (unsigned)o;
+  if (mfast) {
+    const unsigned r = fast_div(uo, fk.fM);
+    m = uo - r * fk.fM.d;
+    b = fast_div(r, fk.fN);
+    n = r - b * fk.fN.d;
+  } else {
+    const unsigned r = fast_div(uo, fk.fN);
+    n = uo - r * fk.fN.d;
+    b = fast_div(r, fk.fM);
+    m = r - b * fk.fM.d;
+  }
+  long long oAb = 0, oBb = 0, oCb = 0, oAm = 0, oCm = 0, oBn = 0, oCn = 0;
+  for (int d = g.nB - 1; d >= 0; --d) {
+    const unsigned q = fast_div(b, fk.fb[d]);
+    const int rr = (int)(b - q * fk.fb[d].d);
+    oAb += rr * g.aB[d];
+    oBb += rr * g.bB[d];
+    oCb += rr * g.cB[d];
+    b = q;
+  }
+  for (int d = g.nM - 1; d >= 0; --d) {
+    const unsigned q = fast_div(m, fk.fm[d]);
+    const int rr = (int)(m - q * fk.fm[d].d);
+    oAm += rr * g.aM[d];
+    oCm += rr * g.cM[d];
+    m = q;
+  }
+  for (int d = g.nN - 1; d >= 0; --d) {
+    const unsigned q = fast_div(n, fk.fn[d]);
+    const int rr = (int)(n - q * fk.fn[d].d);
+    oBn += rr * g.bN[d];
+    oCn += rr * g.cN[d];
+    n = q;
+  }
+  oA = oAb + oAm;
+  oB = oBb + oBn;
+  oC = oCb + oCm + oCn;
+}
+
+template <int WK>
+__global__ void __launch_bounds__(256) k_gemm_flat(const GemmArgs g, const FlatK fk, long long O, int mfast,
+                                                   long long len, double* part) {
+  constexpr int OG = 8 / WK;  // groups of 32 outputs per CTA
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int og = warp / WK, wk = warp - og * WK;
+  const long long o = ((long long)blockIdx.x * OG + og) * 32 + lane;
+  const long long chunk = (long long)blockIdx.y * WK + wk;
+  const long long klo = chunk * len;
+  const long long khi = klo + len < g.K ? klo + len : g.K;
+  double acc = 0.0;
+  long long oA = 0, oB = 0, oC = 0;
+  if (o < O) flat_out(g, fk, o, mfast, oA, oB, oC);
+  if (o < O && klo < khi) {
+    const double* A = g.A + oA;
+    const double* B = g.B + oB;
+    int i0, i1, i2, i3;
+    long long ka, kb;
+    {
+      unsigned lin = (unsigned)klo;
+      unsigned q = fast_div(lin, fk.fk[3]);
+      i3 = (int)(lin - q * fk.fk[3].d);
+      lin = q;
+      q = fast_div(lin, fk.fk[2]);
+      i2 = (int)(lin - q * fk.fk[2].d);
+      lin = q;
+      q = fast_div(lin, fk.fk[1]);
+      i1 = (int)(lin - q * fk.fk[1].d);
+      i0 = (int)q;
+      ka = i0 * fk.a[0] + i1 * fk.a[1] + i2 * fk.a[2] + i3 * fk.a[3];
+      kb = i0 * fk.b[0] + i1 * fk.b[1] + i2 * fk.b[2] + i3 * fk.b[3];
+    }
+    auto step = [&]() {
+      ++i3;
+      ka += fk.a[3];
+      kb += fk.b[3];
+      if (i3 == fk.e[3]) {
+        i3 = 0;
+        ka += fk.wa[3];
+        kb += fk.wb[3];
+        ++i2;
+        if (i2 == fk.e[2]) {
+          i2 = 0;
+          ka += fk.wa[2];
+          kb += fk.wb[2];
+          ++i1;
+          if (i1 == fk.e[1]) {
+            i1 = 0;
+            ka += fk.wa[1];
+            kb += fk.wb[1];
+            ++i0;
+          }
+        }
+      }
+    };
+    long long k = klo;
+    double acc1 = 0.0;
+    for (; k + 4 <= khi; k += 4) {
+      long long pa[4], pb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        pa[u] = ka;
+        pb[u] = kb;
+        step();
+      }
+      double av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        av[u] = __ldg(A + pa[u]);
+        bv[u] = __ldg(B + pb[u]);
+      }
+      acc = fma(av[0], bv[0], acc);
+      acc1 = fma(av[1], bv[1], acc1);
+      acc = fma(av[2], bv[2], acc);
+      acc1 = fma(av[3], bv[3], acc1);
+    }
+    for (; k < khi; ++k) {
+      acc = fma(__ldg(A + ka), __ldg(B + kb), acc);
+      step();
+    }
+    acc += acc1;
+  }
+  if (WK > 1) {
+    __shared__ double sh[8][32];
+    sh[warp][lane] = acc;
+    __syncthreads();
+    if (wk == 0)
+      for (int w = 1; w < WK; ++w) acc += sh[warp + w][lane];
+  }
+  if (wk == 0 && o < O) {
+    if (gridDim.y > 1) part[(long long)blockIdx.y * O + o] = acc;
+    else g.C[oC] += g.alpha * acc;
+  }
+}
+
+// C[o] += alpha * sum_z part[z][o], z in increasing order
+__global__ void k_gemm_flat_reduce(const GemmArgs g, const FlatK fk, long long O, int mfast, int Z,
+                                   const double* part) {
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < O; o += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < Z; ++z) s += part[(long long)z * O + o];
+    long long oA, oB, oC;
+    flat_out(g, fk, o, mfast, oA, oB, oC);
+    g.C[oC] += g.alpha * s;
+  }
+}
+
 // C[m, n] += alpha * sum_z part[z][m][n], z in increasing order
 __global__ void k_gemm_splitk_reduce(const GemmArgs g) {
   const long long MN = g.M * g.N;
@@ -269,11 +438,31 @@ __device__ __forceinline__ void nd_offsets(const NdArgs& g, long long lin, long 
   }
 }
 
+// offsets of linear index lin; FAST: lin < 2^31, divisions by multiply-high
+template <bool FAST>
+__device__ __forceinline__ void nd_off(const NdArgs& g, long long lin, long long& oa, long long& ob) {
+  if (!FAST) {
+    nd_offsets(g, lin, oa, ob);
+    return;
+  }
+  unsigned l = (unsigned)lin;
+  oa = 0;
+  ob = 0;
+  for (int d = g.nd - 1; d >= 0; --d) {
+    const unsigned q = fast_div(l, g.fe[d]);
+    const int r = (int)(l - q * g.fe[d].d);
+    oa += r * g.sa[d];
+    ob += r * g.sb[d];
+    l = q;
+  }
+}
+
+template <bool FAST>
 __global__ void k_axpy(const NdArgs g, double alpha, const double* __restrict__ A, double* __restrict__ C) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.total;
        i += (long long)gridDim.x * blockDim.x) {
     long long oa, oc;
-    nd_offsets(g, i, oa, oc);
+    nd_off<FAST>(g, i, oa, oc);
     C[oc] += alpha * A[oa];
   }
 }
@@ -288,57 +477,74 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
 
 constexpr int DOT_THREADS = 256;
 
-__global__ void __launch_bounds__(DOT_THREADS) k_dot_partial(const NdArgs g, const double* __restrict__ A,
-                                                            const double* __restrict__ B, double* partial) {
+template <bool FAST>
+__global__ void k_axpy_blocks(const NdArgs g, double alpha, const AxpyBlocks p) {
+  const double* __restrict__ A = p.a[blockIdx.y];
+  double* __restrict__ C = p.c[blockIdx.y];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.total;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long oa, oc;
+    nd_off<FAST>(g, i, oa, oc);
+    C[oc] += alpha * A[oa];
+  }
+}
+
+// fixed-order compensated tree over the DOT_THREADS pairs (s, c) in shared memory
+__device__ __forceinline__ void dot_tree(double* sh_s, double* sh_c) {
+  for (int w = DOT_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double s2 = sh_s[threadIdx.x], c2 = sh_c[threadIdx.x];
+      neumaier(s2, c2, sh_s[threadIdx.x + w]);
+      c2 += sh_c[threadIdx.x + w];
+      sh_s[threadIdx.x] = s2;
+      sh_c[threadIdx.x] = c2;
+    }
+    __syncthreads();
+  }
+}
+
+template <bool FAST>
+__global__ void __launch_bounds__(DOT_THREADS) k_dot_blocks(const NdArgs g, const DotBlocks p, double* partial,
+                                                           unsigned* ticket, double alpha, double* out) {
+  const double* __restrict__ A = p.a[blockIdx.y];
+  const double* __restrict__ B = p.b[blockIdx.y];
   double s = 0.0, c = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.total;
        i += (long long)gridDim.x * blockDim.x) {
     long long oa, ob;
-    nd_offsets(g, i, oa, ob);
+    nd_off<FAST>(g, i, oa, ob);
     neumaier(s, c, A[oa] * B[ob]);
   }
   __shared__ double sh_s[DOT_THREADS], sh_c[DOT_THREADS];
+  __shared__ bool last;
   sh_s[threadIdx.x] = s;
   sh_c[threadIdx.x] = c;
   __syncthreads();
-  for (int w = DOT_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      double s2 = sh_s[threadIdx.x], c2 = sh_c[threadIdx.x];
-      neumaier(s2, c2, sh_s[threadIdx.x + w]);
-      c2 += sh_c[threadIdx.x + w];
-      sh_s[threadIdx.x] = s2;
-      sh_c[threadIdx.x] = c2;
-    }
-    __syncthreads();
-  }
+  dot_tree(sh_s, sh_c);
+  const unsigned ncta = gridDim.x * gridDim.y, me = blockIdx.y * gridDim.x + blockIdx.x;
   if (threadIdx.x == 0) {
-    partial[2 * blockIdx.x] = sh_s[0];
-    partial[2 * blockIdx.x + 1] = sh_c[0];
+    partial[2 * me] = sh_s[0];
+    partial[2 * me + 1] = sh_c[0];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == ncta - 1;
   }
-}
-
-__global__ void __launch_bounds__(DOT_THREADS) k_dot_final(const double* partial, int nblk, double alpha,
-                                                          double* out) {
-  double s = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < nblk; i += DOT_THREADS) {
-    neumaier(s, c, partial[2 * i]);
-    c += partial[2 * i + 1];
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  s = 0.0;
+  c = 0.0;
+  for (unsigned i = threadIdx.x; i < ncta; i += DOT_THREADS) {
+    neumaier(s, c, __ldcg(partial + 2 * i));
+    c += __ldcg(partial + 2 * i + 1);
   }
-  __shared__ double sh_s[DOT_THREADS], sh_c[DOT_THREADS];
   sh_s[threadIdx.x] = s;
   sh_c[threadIdx.x] = c;
   __syncthreads();
-  for (int w = DOT_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      double s2 = sh_s[threadIdx.x], c2 = sh_c[threadIdx.x];
-      neumaier(s2, c2, sh_s[threadIdx.x + w]);
-      c2 += sh_c[threadIdx.x + w];
-      sh_s[threadIdx.x] = s2;
-      sh_c[threadIdx.x] = c2;
-    }
-    __syncthreads();
+  dot_tree(sh_s, sh_c);
+  if (threadIdx.x == 0) {
+    *out = alpha * (sh_s[0] + sh_c[0]);
+    *ticket = 0u;
   }
-  if (threadIdx.x == 0) *out = alpha * (sh_s[0] + sh_c[0]);
 }
 
 __global__ void k_fill(double* p, long long n, double v) {
@@ -356,24 +562,31 @@ __device__ __forceinline__ double regulariser(double s, double D) {
   return -expm1(-x) / D;
 }
 
+// One thread per spatial (a, b, i, j): D and R(D) once, then the 16 spin
+// blocks (sa, sb, si, sj) of the [2p][2p][2h][2h] arrays; blocks that change
+// the number of alpha electrons are written as zeros.  Consecutive threads
+// take consecutive j (contiguous within a spin block).
 __global__ void k_amp2(int nc, int na, int nv, double s, const double* __restrict__ eps,
                        const double* __restrict__ O2, double* __restrict__ T2, double* __restrict__ W2) {
   const int h = nc + na, p = na + nv;
+  const unsigned hh = (unsigned)h * h, total = (unsigned)p * p * hh;
   const long long P2 = 2LL * p, H2 = 2LL * h;
-  const long long total = P2 * P2 * H2 * H2;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long r = idx;
-    int j = (int)(r % H2); r /= H2;
-    int i = (int)(r % H2); r /= H2;
-    int b = (int)(r % P2); r /= P2;
-    int a = (int)r;
-    int ja = j % h, ia = i % h, bb = b % p, aa = a % p;
-    bool internal = (ja >= nc) && (ia >= nc) && (bb < na) && (aa < na);
-    double D = eps[ia] + eps[ja] - eps[nc + aa] - eps[nc + bb];
-    double t = internal ? 0.0 : O2[idx] * regulariser(s, D);
-    T2[idx] = t;
-    if (W2) W2[idx] = -D * t;
+  for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const unsigned ab = idx / hh, ij = idx - ab * hh;
+    const int a = (int)(ab / p), b = (int)(ab - (unsigned)a * p);
+    const int i = (int)(ij / h), j = (int)(ij - (unsigned)i * h);
+    const bool internal = (i >= nc) && (j >= nc) && (a < na) && (b < na);
+    const double D = eps[i] + eps[j] - eps[nc + a] - eps[nc + b];
+    const double R = internal ? 0.0 : regulariser(s, D);
+#pragma unroll
+    for (int sp = 0; sp < 16; ++sp) {
+      const int sa = sp >> 3 & 1, sb = sp >> 2 & 1, si = sp >> 1 & 1, sj = sp & 1;
+      const long long o = (((sa * p + a) * P2 + (sb * p + b)) * H2 + (si * h + i)) * H2 + (sj * h + j);
+      double t = 0.0;
+      if (sa + sb == si + sj) t = O2[o] * R;
+      T2[o] = t;
+      if (W2) W2[o] = -D * t;
+    }
   }
 }
 
@@ -505,6 +718,69 @@ bool gemm_is_short(const GemmArgs& g) {
   return g.K <= TPO_KMAX && g.M < (1LL << 31) && g.N < (1LL << 31) && !gemm_is_small(g);
 }
 
+bool gemm_use_flat(const GemmArgs& g) {
+  const long long O = g.M * g.N * g.nbatch;
+  if (O >= (1LL << 31) || g.K >= (1LL << 31) || g.M >= (1LL << 31) || g.N >= (1LL << 31)) return false;
+  // full-size tiles with enough of them keep the register-blocked kernel
+  const long long tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64) * g.nbatch;
+  return !(g.M >= 64 && g.N >= 64 && g.K > 64 && tiles >= 2 * 152);
+}
+
+FlatPlan gemm_flat_plan(const GemmArgs& g) {
+  FlatPlan p{};
+  const long long O = g.M * g.N * g.nbatch;
+  // about 32 resident warps per SM: enough FMAs in flight to cover latency
+  const long long target = 152LL * 1024;
+  long long chunks = (target + O - 1) / O;
+  const long long maxc = g.K / 16 > 1 ? g.K / 16 : 1;  // at least 16 k per chunk
+  if (chunks > maxc) chunks = maxc;
+  if (chunks < 1) chunks = 1;
+  p.wk = chunks >= 8 ? 8 : chunks >= 4 ? 4 : chunks >= 2 ? 2 : 1;
+  long long z = (chunks + p.wk - 1) / p.wk;
+  if (z > 65535) z = 65535;
+  p.len = (g.K + p.wk * z - 1) / (p.wk * z);
+  p.z = (int)((g.K + p.len * p.wk - 1) / (p.len * p.wk));
+  // lanes walk the output index whose operand stride is smallest
+  const long long sm = g.nM ? (g.aM[g.nM - 1] < g.cM[g.nM - 1] ? g.aM[g.nM - 1] : g.cM[g.nM - 1]) : (1LL << 62);
+  const long long sn = g.nN ? (g.bN[g.nN - 1] < g.cN[g.nN - 1] ? g.bN[g.nN - 1] : g.cN[g.nN - 1]) : (1LL << 62);
+  p.mfast = sm < sn ? 1 : 0;
+  return p;
+}
+
+void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, double* part, cudaStream_t st) {
+  const long long O = g.M * g.N * g.nbatch;
+  if (O <= 0 || g.K <= 0) return;
+  FlatK fk{};
+  const int pad = 4 - g.nK;
+  for (int d = 0; d < 4; ++d) {
+    const int s = d - pad;
+    fk.e[d] = s >= 0 ? g.eK[s] : 1;
+    fk.a[d] = s >= 0 ? g.aK[s] : 0;
+    fk.b[d] = s >= 0 ? g.bK[s] : 0;
+  }
+  for (int d = 1; d < 4; ++d) {
+    fk.wa[d] = fk.a[d - 1] - (long long)fk.e[d] * fk.a[d];
+    fk.wb[d] = fk.b[d - 1] - (long long)fk.e[d] * fk.b[d];
+  }
+  for (int d = 0; d < 4; ++d) {
+    fk.fk[d] = make_fastdiv((unsigned)fk.e[d]);
+    fk.fm[d] = make_fastdiv(d < g.nM ? (unsigned)g.eM[d] : 1u);
+    fk.fn[d] = make_fastdiv(d < g.nN ? (unsigned)g.eN[d] : 1u);
+    fk.fb[d] = make_fastdiv(d < g.nB ? (unsigned)g.eB[d] : 1u);
+  }
+  fk.fM = make_fastdiv((unsigned)g.M);
+  fk.fN = make_fastdiv((unsigned)g.N);
+  const long long per_cta = 32LL * (8 / p.wk);
+  dim3 grid((unsigned)((O + per_cta - 1) / per_cta), (unsigned)p.z);
+  switch (p.wk) {
+    case 8: k_gemm_flat<8><<<grid, 256, 0, st>>>(g, fk, O, p.mfast, p.len, part); break;
+    case 4: k_gemm_flat<4><<<grid, 256, 0, st>>>(g, fk, O, p.mfast, p.len, part); break;
+    case 2: k_gemm_flat<2><<<grid, 256, 0, st>>>(g, fk, O, p.mfast, p.len, part); break;
+    default: k_gemm_flat<1><<<grid, 256, 0, st>>>(g, fk, O, p.mfast, p.len, part); break;
+  }
+  if (p.z > 1) k_gemm_flat_reduce<<<grid_for(O, 256), 256, 0, st>>>(g, fk, O, p.mfast, p.z, part);
+}
+
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nbatch <= 0) return;
   int bm, bn;
@@ -535,16 +811,41 @@ void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind) {
   if (g.splits > 1) k_gemm_splitk_reduce<<<grid_for(g.M * g.N, 256), 256, 0, st>>>(g);
 }
 
-void launch_axpy(const NdArgs& g, double alpha, const double* A, double* C, cudaStream_t st) {
-  if (g.total <= 0) return;
-  k_axpy<<<grid_for(g.total, 256), 256, 0, st>>>(g, alpha, A, C);
+namespace {
+// fills the fast divisors; true when every linear index fits 31 bits
+bool nd_prepare(NdArgs& g) {
+  if (g.total >= (1LL << 31)) return false;
+  for (int d = 0; d < g.nd; ++d) g.fe[d] = make_fastdiv((unsigned)g.e[d]);
+  return true;
+}
+}  // namespace
+
+void launch_axpy(const NdArgs& g0, double alpha, const double* A, double* C, cudaStream_t st) {
+  if (g0.total <= 0) return;
+  NdArgs g = g0;
+  if (nd_prepare(g)) k_axpy<true><<<grid_for(g.total, 256), 256, 0, st>>>(g, alpha, A, C);
+  else k_axpy<false><<<grid_for(g.total, 256), 256, 0, st>>>(g, alpha, A, C);
 }
 
-void launch_dot(const NdArgs& g, double alpha, const double* A, const double* B, double* scratch,
-                int scratch_len, double* out_slot, cudaStream_t st) {
-  int nblk = grid_for(g.total, DOT_THREADS, scratch_len / 2);
-  k_dot_partial<<<nblk, DOT_THREADS, 0, st>>>(g, A, B, scratch);
-  k_dot_final<<<1, DOT_THREADS, 0, st>>>(scratch, nblk, alpha, out_slot);
+void launch_axpy_blocks(const NdArgs& g0, double alpha, const AxpyBlocks& p, cudaStream_t st) {
+  if (g0.total <= 0 || p.n <= 0) return;
+  NdArgs g = g0;
+  const int gx = grid_for(g.total, 256, (152 * 16 + p.n - 1) / p.n);
+  const dim3 grid((unsigned)gx, (unsigned)p.n);
+  if (nd_prepare(g)) k_axpy_blocks<true><<<grid, 256, 0, st>>>(g, alpha, p);
+  else k_axpy_blocks<false><<<grid, 256, 0, st>>>(g, alpha, p);
+}
+
+void launch_dot_blocks(const NdArgs& g0, double alpha, const DotBlocks& p, double* scratch, int scratch_len,
+                       unsigned* ticket, double* out, cudaStream_t st) {
+  if (p.n <= 0) return;
+  NdArgs g = g0;
+  int cap = scratch_len / 2 / p.n;
+  if (cap < 1) throw std::runtime_error("dot: scratch too small for the spin blocks");
+  const int gx = grid_for(g.total > 0 ? g.total : 1, DOT_THREADS, cap);
+  const dim3 grid((unsigned)gx, (unsigned)p.n);
+  if (nd_prepare(g)) k_dot_blocks<true><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
+  else k_dot_blocks<false><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
 }
 
 void launch_fill(double* p, long long n, double v, cudaStream_t st) {
@@ -570,7 +871,8 @@ void launch_build_cumulant(int na, int rank, const double* const* blk_dev, doubl
 void launch_amp2(int nc, int na, int nv, double s, const double* eps, const double* O2, double* T2, double* W2,
                  cudaStream_t st) {
   long long h = nc + na, p = na + nv;
-  long long n = 16 * p * p * h * h;
+  long long n = p * p * h * h;  // spatial quadruples, one thread each
+  if (n >= (1LL << 32)) throw std::runtime_error("amplitudes: p^2 h^2 must stay below 2^32");
   k_amp2<<<grid_for(n, 256), 256, 0, st>>>(nc, na, nv, s, eps, O2, T2, W2);
 }
 

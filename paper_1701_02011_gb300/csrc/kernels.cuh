@@ -11,6 +11,31 @@ namespace dsrg {
 
 constexpr int kMaxDims = 8;
 
+// Division by a run-time invariant divisor d >= 1 through a multiply-high
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, round-up variant): with l = ceil(log2 d) and
+// m = floor(2^(32+l) / d) + 1 = 2^32 + mlo, floor(n / d) = floor(m n / 2^(32+l))
+// for every 32-bit n.  Index decoding in the element-wise, reduction and flat
+// contraction kernels uses it instead of the long instruction sequence of a
+// general integer division.
+struct FastDiv {
+  unsigned d, mlo;
+  int l;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f{};
+  f.d = d ? d : 1;
+  f.l = 0;
+  while ((1ull << f.l) < f.d) ++f.l;
+  f.mlo = (unsigned)(((1ull << 32) * ((1ull << f.l) - f.d)) / f.d + 1);
+  return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fast_div(unsigned n, const FastDiv& f) {
+  return (unsigned)(((unsigned long long)__umulhi(n, f.mlo) + n) >> f.l);
+}
+#endif
+
 // C[m, n] += alpha * sum_k A[m, k] B[k, n] over multi-indices m, n, k and a
 // batch multi-index b present in all three operands.  Every group holds up
 // to four dimensions with an extent and one stride per operand.
@@ -37,6 +62,7 @@ struct GemmArgs {
 struct NdArgs {
   int nd;
   int e[kMaxDims];
+  FastDiv fe[kMaxDims];  // filled by the launchers when total < 2^31
   long long sa[kMaxDims];
   long long sb[kMaxDims];
   long long total;
@@ -44,9 +70,26 @@ struct NdArgs {
 
 // C[idx] += alpha * A[idx] (strides sb for C, sa for A).
 void launch_axpy(const NdArgs& g, double alpha, const double* A, double* C, cudaStream_t st);
-// partial[slot] = alpha * sum A[idx] * B[idx]; deterministic two-pass reduction.
-void launch_dot(const NdArgs& g, double alpha, const double* A, const double* B,
-                double* scratch, int scratch_len, double* out_slot, cudaStream_t st);
+
+// Up to kMaxBlocks spin blocks sharing extents and strides, one launch.
+constexpr int kMaxBlocks = 64;
+struct AxpyBlocks {
+  const double* a[kMaxBlocks];
+  double* c[kMaxBlocks];
+  int n;
+};
+struct DotBlocks {
+  const double* a[kMaxBlocks];
+  const double* b[kMaxBlocks];
+  int n;
+};
+// C_k[idx] += alpha * A_k[idx] for every block k (distinct C blocks)
+void launch_axpy_blocks(const NdArgs& g, double alpha, const AxpyBlocks& p, cudaStream_t st);
+// *out = alpha * sum_k sum_idx A_k[idx] B_k[idx] in one launch: per-CTA
+// compensated partials, and the CTA that finishes last (atomic ticket, reset
+// afterwards; no CTA waits) adds them in a fixed order.
+void launch_dot_blocks(const NdArgs& g, double alpha, const DotBlocks& p, double* scratch, int scratch_len,
+                       unsigned* ticket, double* out, cudaStream_t st);
 // Output tile of the generic contraction for an M x N output (kinds 1, 2
 // always use 64 x 64).
 void gemm_tile(long long M, long long N, int* bm, int* bn);
@@ -54,6 +97,17 @@ void gemm_tile(long long M, long long N, int* bm, int* bn);
 bool gemm_is_small(const GemmArgs& g);
 // true when K is short enough for one thread per output element
 bool gemm_is_short(const GemmArgs& g);
+// Flat contraction (one thread per output and k chunk, no tile padding) for
+// narrow, short or small products.  A plan with z > 1 needs part[z * M*N*nbatch].
+struct FlatPlan {
+  int wk;         // warps of a CTA on consecutive k chunks of the same outputs (1, 2, 4, 8)
+  int z;          // CTA rows over k (partials reduced in a fixed order)
+  long long len;  // k per chunk
+  int mfast;      // lanes along m (1) or n (0)
+};
+bool gemm_use_flat(const GemmArgs& g);
+FlatPlan gemm_flat_plan(const GemmArgs& g);
+void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, double* part, cudaStream_t st);
 // kind 0: generic contraction, 1: DF build of (pr|qs), 2: ladder contraction
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind = 0);
 void launch_fill(double* p, long long n, double v, cudaStream_t st);

@@ -13,6 +13,8 @@ constexpr int OZ_BM = 128, OZ_BK = 64;
 constexpr int OZ_THREADS = 256;  // 8 warps: lane quadrant (warp % 4) x column half (warp / 4)
 constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // A tile: 8192 bf16 = 16 KiB
 constexpr int OZ_TILE_BYTES = OZ_TILE_ELEMS * 2;
+// exponents are stored as 2048 + frexp exponent of the row / column maximum (0: all zero)
+constexpr unsigned OZ_EBIAS = 2048;
 constexpr long long OZ_WAIT_LIMIT = 1LL << 22;
 
 __device__ int g_oz_status;
@@ -129,6 +131,7 @@ struct OzArgs {
   int nM, nN;
   int eM[4], eN[4];
   long long cM[4], cN[4];
+  int rowfast;  // C's row index has the smaller stride (epilogue writes along rows)
   int* status;
   // split over k tiles: CTA z covers [z*ktper, (z+1)*ktper) and writes its
   // scaled partial tile to part[z][MT*128][NT*BN] instead of C
@@ -146,8 +149,24 @@ __device__ __forceinline__ long long c_offset(long long lin, int nd, const int* 
   return o;
 }
 
-// One CTA: a 128 x BN tile of C.  Thread t owns TMEM lane t (tile row t).
-// TMEM columns: level accumulator [0,BN), running hi [BN,2BN), lo [2BN,3BN).
+// (double)f * 2^k assembled from the bit pattern of the float f (sign,
+// re-biased exponent, mantissa) with integer instructions; zero gives zero and
+// subnormal, non-finite or out-of-range cases take the library path.
+__device__ __forceinline__ double f32_to_f64_scaled(uint32_t u, int k) {
+  if ((u << 1) == 0) return 0.0;
+  const uint32_t ex = (u >> 23) & 0xFFu;
+  const int e = (int)ex - 127 + 1023 + k;
+  if (ex == 0 || ex == 255 || e <= 0 || e >= 2047) return ldexp((double)__uint_as_float(u), k);
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)e << 52) |
+                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// One CTA: a 128 x BN tile of C with 8 warps; warp w reads TMEM lanes
+// 32 (w % 4) .. (tile rows) and column half w / 4.  Per k tile, thread 0
+// issues the MMAs of level c + 1 into one TMEM accumulator while all warps
+// fold level c out of the other one; the next k tile's bulk copies start as
+// soon as the last level's MMAs have completed.
 template <int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   constexpr uint32_t TMEM_COLS = BN == 128 ? 512 : BN == 64 ? 256 : 128;
@@ -160,9 +179,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
   unsigned char* sB = smem + (size_t)a.S * OZ_TILE_BYTES;
-  __shared__ uint64_t bar_mma, bar_load;
+  __shared__ uint64_t bar_mma[2], bar_load;
   __shared__ uint32_t tmem_base;
-  __shared__ long long colC[BN];
+  __shared__ long long colC[BN], rowC[OZ_BM];
   __shared__ int colE[BN];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32*quad.., columns half*HALF..
@@ -178,14 +197,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bar_mma, 1);
+    mbar_init(&bar_mma[0], 1);
+    mbar_init(&bar_mma[1], 1);
     mbar_init(&bar_load, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int t = tid; t < BN; t += OZ_THREADS) {
     long long n = (long long)nt * BN + t;
     colC[t] = n < a.N ? c_offset(n, a.nN, a.eN, a.cN) : -1;
-    colE[t] = a.fb[(long long)nt * BN + t];
+    colE[t] = a.fb[(long long)nt * BN + t] - (int)OZ_EBIAS;
+  }
+  for (int t = tid; t < OZ_BM; t += OZ_THREADS) {
+    long long m = (long long)mt * OZ_BM + t;
+    rowC[t] = m < a.M ? c_offset(m, a.nM, a.eM, a.cM) : -1;
   }
   tc_fence_before();
   __syncthreads();
@@ -195,66 +219,95 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   const uint32_t col0 = (uint32_t)(half * HALF);
   const int nchunk = (BN >= 64 || half == 0) ? HALF / 32 : 0;  // 32-column chunks of this warp
 
-  // zero the running float-float sums (hi, lo) of this thread's columns
+  // TMEM columns: level accumulators [0, BN) and [BN, 2BN) (levels alternate),
+  // running float-float sum hi [2BN, 3BN) and lo [3BN, 4BN)
+  constexpr uint32_t HI = 2 * BN, LO = 3 * BN;
+  static_assert(4 * BN <= (int)TMEM_COLS, "TMEM columns");
   {
     uint32_t zr[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) zr[q] = 0u;
 #pragma unroll
     for (int j = 0; j < nchunk; ++j) {
-      tmem_st32(tm + lane_off + BN + col0 + 32 * j, zr);
-      tmem_st32(tm + lane_off + 2 * BN + col0 + 32 * j, zr);
+      tmem_st32(tm + lane_off + HI + col0 + 32 * j, zr);
+      tmem_st32(tm + lane_off + LO + col0 + 32 * j, zr);
     }
     tmem_wait_st();
   }
-  uint32_t ph_mma = 0, ph_load = 0;
-  bool ok = true;
-  const int S = a.S;
-  for (int kt = kt0; kt < kt1 && ok; ++kt) {
-    // stage the S digit tiles of A and of B for this k chunk (bulk copies)
-    if (tid == 0) {
-      mbar_expect_tx(&bar_load, (uint32_t)(S * (OZ_TILE_BYTES + B_TILE_BYTES)));
-      for (int s = 0; s < S; ++s) {
-        bulk_g2s(sA + (size_t)s * OZ_TILE_BYTES, a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS,
-                 OZ_TILE_BYTES, &bar_load);
-        bulk_g2s(sB + (size_t)s * B_TILE_BYTES, a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * (BN * OZ_BK),
-                 B_TILE_BYTES, &bar_load);
+  const int S = a.S, L = S + 1;  // levels c = 2 .. S + 1
+  // thread 0: bulk copies of the S digit tiles of A and of B for k tile kt
+  auto issue_loads = [&](int kt) {
+    mbar_expect_tx(&bar_load, (uint32_t)(S * (OZ_TILE_BYTES + B_TILE_BYTES)));
+    for (int s = 0; s < S; ++s) {
+      bulk_g2s(sA + (size_t)s * OZ_TILE_BYTES, a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS,
+               OZ_TILE_BYTES, &bar_load);
+      bulk_g2s(sB + (size_t)s * B_TILE_BYTES, a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * (BN * OZ_BK),
+               B_TILE_BYTES, &bar_load);
+    }
+  };
+  // thread 0: the MMAs of level c (pairs t + u = c) into accumulator c & 1
+  auto issue_level = [&](int c) {
+    const uint32_t d = tm + (uint32_t)((c & 1) * BN);
+    uint32_t accum = 0;
+    const int t0 = c - S > 1 ? c - S : 1, t1 = c - 1 < S ? c - 1 : S;
+    for (int t = t0; t <= t1; ++t) {
+      const int u = c - t;
+      const uint32_t aA = smem_u32(sA + (size_t)(t - 1) * OZ_TILE_BYTES);
+      const uint32_t aB = smem_u32(sB + (size_t)(u - 1) * B_TILE_BYTES);
+#pragma unroll
+      for (int ks = 0; ks < OZ_BK / 16; ++ks) {
+        mma_bf16(d, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), IDESC, accum);
+        accum = 1;
       }
     }
+    mma_commit(&bar_mma[c & 1]);
+  };
+  uint32_t ph_mma[2] = {0, 0}, ph_load = 0;
+  bool load_pending = false, mma_pending[2] = {false, false};  // meaningful in thread 0
+  bool ok = true;
+  if (tid == 0 && kt0 < kt1) {
+    issue_loads(kt0);
+    load_pending = true;
+  }
+  for (int kt = kt0; kt < kt1 && ok; ++kt) {
     ok = mbar_wait(&bar_load, ph_load);
-    ph_load ^= 1;
+    if (ok) ph_load ^= 1;  // a timed-out wait keeps its parity for the second wait
+    if (tid == 0 && ok) load_pending = false;
     ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
-    for (int c = 2; c <= S + 1 && ok; ++c) {
-      if (tid == 0) {
-        uint32_t accum = 0;
-        const int t0 = c - S > 1 ? c - S : 1, t1 = c - 1 < S ? c - 1 : S;
-        for (int t = t0; t <= t1; ++t) {
-          const int u = c - t;
-          const uint32_t aA = smem_u32(sA + (size_t)(t - 1) * OZ_TILE_BYTES);
-          const uint32_t aB = smem_u32(sB + (size_t)(u - 1) * B_TILE_BYTES);
-#pragma unroll
-          for (int ks = 0; ks < OZ_BK / 16; ++ks) {
-            mma_bf16(tm, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), IDESC, accum);
-            accum = 1;
-          }
-        }
-        mma_commit(&bar_mma);
-      }
-      ok = mbar_wait(&bar_mma, ph_mma);
-      ph_mma ^= 1;
-      ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    if (tid == 0) {
+      issue_level(2);
+      mma_pending[0] = true;
+    }
+    for (int c = 2; c <= L; ++c) {
+      // level c complete; start level c + 1 in the other accumulator (folded
+      // before the last barrier), or, after the last level, the next k tile
+      bool w = mbar_wait(&bar_mma[c & 1], ph_mma[c & 1]);
+      if (w) ph_mma[c & 1] ^= 1;
+      if (tid == 0 && w) mma_pending[c & 1] = false;
+      ok = __syncthreads_and(w) != 0;
       tc_fence_after();
       if (!ok) break;
+      if (tid == 0) {
+        if (c < L) {
+          issue_level(c + 1);
+          mma_pending[(c + 1) & 1] = true;
+        } else if (kt + 1 < kt1) {
+          issue_loads(kt + 1);
+          load_pending = true;
+        }
+      }
       // fold level c: (hi, lo) += acc * 2^(-7c), two-sum in FP32
       const float scale = exp2f(-7.0f * (float)c);
+      const uint32_t src = (uint32_t)((c & 1) * BN);
 #pragma unroll 1
       for (int j = 0; j < nchunk; ++j) {
         uint32_t acc[32], hi[32], lo[32];
         const uint32_t cc = col0 + 32 * j;
-        tmem_ld32(tm + lane_off + cc, acc);
-        tmem_ld32(tm + lane_off + BN + cc, hi);
-        tmem_ld32(tm + lane_off + 2 * BN + cc, lo);
+        tmem_ld32(tm + lane_off + src + cc, acc);
+        tmem_ld32(tm + lane_off + HI + cc, hi);
+        tmem_ld32(tm + lane_off + LO + cc, lo);
         tmem_wait_ld();
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
@@ -269,8 +322,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
           hi[q] = __float_as_uint(s2);
           lo[q] = __float_as_uint(l);
         }
-        tmem_st32(tm + lane_off + BN + cc, hi);
-        tmem_st32(tm + lane_off + 2 * BN + cc, lo);
+        tmem_st32(tm + lane_off + HI + cc, hi);
+        tmem_st32(tm + lane_off + LO + cc, lo);
       }
       tmem_wait_st();
       tc_fence_before();
@@ -278,35 +331,74 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
       tc_fence_after();
     }
   }
-  // epilogue: alpha * 2^(ea[m] + fb[n]) * (hi + lo) into C, or the scaled
-  // partial into part[z] when K is split
+  // after a timed-out wait: give the copies and MMAs still in flight a second
+  // bounded wait before the shared memory and TMEM are released
+  if (!ok && tid == 0) {
+    if (load_pending) mbar_wait(&bar_load, ph_load);
+    for (int i = 0; i < 2; ++i)
+      if (mma_pending[i]) mbar_wait(&bar_mma[i], ph_mma[i]);
+  }
+  // epilogue: the scaled tile 2^(ea[m] + fb[n]) (hi + lo) goes to shared
+  // memory (the operand tiles are free once the last MMA has completed; rows
+  // padded by one double against bank conflicts), then consecutive threads
+  // write consecutive columns of C (alpha times, accumulated) or of the
+  // split-k partial part[z]
+  constexpr int LDT = BN + 1;
+  double* stile = reinterpret_cast<double*>(smem);
   if (ok) {
-    const long long m = (long long)mt * OZ_BM + row;
-    const long long offm = m < a.M ? c_offset(m, a.nM, a.eM, a.cM) : -1;
-    const int em = a.ea[(long long)mt * OZ_BM + row];
-    const long long ldp = (long long)a.NT * BN;
-    double* prow = a.splits > 1 ? a.part + ((long long)z * a.MT * OZ_BM + m) * ldp + (long long)nt * BN : nullptr;
+    const int em = a.ea[(long long)mt * OZ_BM + row] - (int)OZ_EBIAS;
 #pragma unroll 1
     for (int j = 0; j < nchunk; ++j) {
       uint32_t hi[32], lo[32];
       const int cc = (int)col0 + 32 * j;
-      tmem_ld32(tm + lane_off + BN + cc, hi);
-      tmem_ld32(tm + lane_off + 2 * BN + cc, lo);
+      tmem_ld32(tm + lane_off + 2 * BN + cc, hi);
+      tmem_ld32(tm + lane_off + 3 * BN + cc, lo);
       tmem_wait_ld();
-      if (prow) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          double v = (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]);
-          prow[cc + q] = colC[cc + q] >= 0 && offm >= 0 ? ldexp(v, em + colE[cc + q]) : 0.0;
-        }
-      } else if (offm >= 0) {
+      for (int q = 0; q < 32; ++q) {
+        const int k = em + colE[cc + q];
+        stile[row * LDT + cc + q] = f32_to_f64_scaled(hi[q], k) + f32_to_f64_scaled(lo[q], k);
+      }
+    }
+  }
+  __syncthreads();
+  if (ok) {
+    if (a.splits > 1) {
+      const long long ldp = (long long)a.NT * BN;
+      double* pz = a.part + ((long long)z * a.MT * OZ_BM + (long long)mt * OZ_BM) * ldp + (long long)nt * BN;
+      for (int i = tid; i < OZ_BM * BN; i += OZ_THREADS) {
+        const int r = i / BN, c = i - r * BN;
+        const bool live = (long long)mt * OZ_BM + r < a.M && colC[c] >= 0;
+        pz[(long long)r * ldp + c] = live ? stile[r * LDT + c] : 0.0;
+      }
+    } else {
+      // eight read-modify-writes per thread with all loads issued first;
+      // consecutive threads on C's contiguous index (rows when rowfast)
+      constexpr int U = 8;
+      static_assert((OZ_BM * BN) % (U * OZ_THREADS) == 0, "epilogue tiling");
+      for (int base = 0; base < OZ_BM * BN; base += U * OZ_THREADS) {
+        long long off[U];
+        double cv[U], tv[U];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const long long oc = colC[cc + q];
-          if (oc < 0) continue;
-          double v = (double)__uint_as_float(hi[q]) + (double)__uint_as_float(lo[q]);
-          a.C[offm + oc] += a.alpha * ldexp(v, em + colE[cc + q]);
+        for (int u = 0; u < U; ++u) {
+          const int i = base + u * OZ_THREADS + tid;
+          int r, c;
+          if (a.rowfast) {
+            c = i / OZ_BM;
+            r = i - c * OZ_BM;
+          } else {
+            r = i / BN;
+            c = i - r * BN;
+          }
+          const long long oc = colC[c], orow = rowC[r];
+          off[u] = oc >= 0 && orow >= 0 ? orow + oc : -1;
+          tv[u] = stile[r * LDT + c];
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) cv[u] = off[u] >= 0 ? a.C[off[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (off[u] >= 0) a.C[off[u]] = cv[u] + a.alpha * tv[u];
       }
     }
   }
@@ -343,94 +435,195 @@ struct OzPack {
   int T, KT;           // tiles along rows (TR each) and k (64 each)
   int TR;              // rows per tile: 128 (A) or BN (B)
   int S;
+  FastDiv fR[4], fK[4];  // divisors of eR, eK
 };
 
-__device__ __forceinline__ long long src_offset32(int lin, int nd, const int* ext, const long long* st) {
-  long long o = 0;
-  for (int d = nd - 1; d >= 0; --d) {
-    int q = lin / ext[d];
-    o += (long long)(lin - q * ext[d]) * st[d];
-    lin = q;
-  }
-  return o;
-}
-
-// One CTA per row r (rows beyond R and rows of padding write zeros):
-// e[r] = max over k of the binary exponent ex with |x| < 2^ex (frexp), then
-// the S digits of every element of the row go to their swizzled tile slots.
+// Operand preparation runs in two passes over the padded operand viewed as
+// rows x (8-element k groups).  Work item i is one (row r, group q); when the
+// source's innermost k index is contiguous the groups of a row are adjacent
+// items (reads coalesce along k), otherwise the rows are (reads coalesce along
+// the row index).
+//   pass 1: eu[r] = 2048 + max over k of the binary exponent ex with
+//           |x| < 2^ex (frexp), 0 for an all-zero row (eu zeroed beforehand);
+//   pass 2: the S signed 7-bit digits of x 2^(-e) go to the swizzled tiles,
+//           eight bf16 (16 bytes) per store.
 constexpr int PACK_T = 256;
 
-__device__ __forceinline__ int exp_of(double x) {
-  if (x == 0.0) return -2000;
-  const long long bits = __double_as_longlong(x);
+// Everything below works on the bit patterns with integer instructions: the
+// FP64 pipe of this SM is narrow, and even a comparison with 0.0 runs there.
+__device__ __forceinline__ unsigned exp_code(long long bits) {
+  if ((bits << 1) == 0) return 0u;  // +-0
   const int be = (int)((bits >> 52) & 0x7FF);
-  return be ? be - 1022 : -1022;
+  return (unsigned)((be ? be - 1022 : -1022) + (int)OZ_EBIAS);
 }
 
-__global__ void __launch_bounds__(PACK_T) k_ozaki_pack(const OzPack p, int* e_out, __nv_bfloat16* dst) {
-  const int r = blockIdx.x;  // over T * TR rows (padded)
-  const long long Kp = (long long)p.KT * OZ_BK;
-  const bool live = r < p.R;
-  const long long roff = live ? src_offset32(r, p.nR, p.eR, p.sR) : 0;
-  // row maximum exponent
-  int emax = -2000;
-  if (live)
-    for (int k = threadIdx.x; k < p.K; k += PACK_T) {
-      const int ex = exp_of(p.src[roff + src_offset32(k, p.nK, p.eK, p.sK)]);
-      emax = ex > emax ? ex : emax;
-    }
-  __shared__ int sh[PACK_T / 32];
-  for (int o = 16; o > 0; o >>= 1) {
-    const int v = __shfl_xor_sync(0xffffffffu, emax, o);
-    emax = v > emax ? v : emax;
+// work item i -> (row r, group q); i, Rpad, Q < 2^32
+__device__ __forceinline__ void pack_item(unsigned i, const FastDiv& fQ, const FastDiv& fR, bool kfast, unsigned& r,
+                                          unsigned& q) {
+  if (kfast) {
+    r = fast_div(i, fQ);
+    q = i - r * fQ.d;
+  } else {
+    q = fast_div(i, fR);
+    r = i - q * fR.d;
   }
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = emax;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    int v = threadIdx.x < PACK_T / 32 ? sh[threadIdx.x] : -2000;
-    for (int o = 16; o > 0; o >>= 1) {
-      const int w = __shfl_xor_sync(0xffffffffu, v, o);
-      v = w > v ? w : v;
+}
+
+// bit patterns of the (up to) 8 source values of group q of row r; zero
+// outside R x K
+__device__ __forceinline__ void pack_load8(const OzPack& p, unsigned r, unsigned q, long long x[8]) {
+  const unsigned k0 = q * 8u;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 0;
+  if (r >= (unsigned long long)p.R || k0 >= (unsigned long long)p.K) return;
+  const long long* src = reinterpret_cast<const long long*>(p.src);
+  long long roff = 0;
+  {
+    unsigned lin = r;
+    for (int d = p.nR - 1; d >= 0; --d) {
+      const unsigned qd = fast_div(lin, p.fR[d]);
+      roff += (long long)(lin - qd * p.fR[d].d) * p.sR[d];
+      lin = qd;
     }
-    if (threadIdx.x == 0) sh[0] = v;
   }
-  __syncthreads();
-  const int e = sh[0];
-  if (threadIdx.x == 0) e_out[r] = e;
-  const int F = 7 * p.S;
-  const long long tile_elems = (long long)p.TR * OZ_BK;
-  const int tr = r / p.TR, rr = r - tr * p.TR;
-  for (long long k = threadIdx.x; k < Kp; k += PACK_T) {
-    double x = 0.0;
-    if (live && k < p.K) x = p.src[roff + src_offset32((int)k, p.nK, p.eK, p.sK)];
-    unsigned long long v = 0;
-    bool neg = false;
-    if (x != 0.0) {
-      const long long bits = __double_as_longlong(x);
-      neg = bits < 0;
-      const int be = (int)((bits >> 52) & 0x7FF);
-      unsigned long long m = (unsigned long long)(bits & ((1LL << 52) - 1));
-      int E;
-      if (be) {
-        m |= 1ULL << 52;
-        E = be - 1075;
-      } else {
-        E = -1074;
+  // multi-index of k0, then step through the next 7 with carries
+  int idx[4];
+  long long off = 0;
+  {
+    unsigned lin = k0;
+    for (int d = p.nK - 1; d >= 0; --d) {
+      const unsigned qd = fast_div(lin, p.fK[d]);
+      idx[d] = (int)(lin - qd * p.fK[d].d);
+      off += (long long)idx[d] * p.sK[d];
+      lin = qd;
+    }
+  }
+  const int last = p.nK - 1;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (k0 + j >= (unsigned long long)p.K) break;
+    x[j] = src[roff + off];
+    if (j == 7) break;
+    int d = last;
+    ++idx[d];
+    off += p.sK[d];
+    while (idx[d] == p.eK[d] && d > 0) {
+      off -= (long long)p.eK[d] * p.sK[d];
+      idx[d] = 0;
+      --d;
+      ++idx[d];
+      off += p.sK[d];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const OzPack p, unsigned* eu, int kfast, FastDiv fQ,
+                                                         FastDiv fR, unsigned W) {
+  const unsigned stride = gridDim.x * PACK_T;
+  for (unsigned base = blockIdx.x * PACK_T; base < W; base += stride) {
+    const unsigned i = base + threadIdx.x;
+    unsigned v = 0;
+    long long r = -1;
+    if (i < W) {
+      unsigned rr, q;
+      pack_item(i, fQ, fR, kfast != 0, rr, q);
+      if (rr < (unsigned long long)p.R) {
+        long long x[8];
+        pack_load8(p, rr, q, x);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const unsigned c = exp_code(x[j]);
+          v = c > v ? c : v;
+        }
+        r = rr;
       }
-      const int sh_ = E + F - e;  // v = m 2^sh < 2^F
-      if (sh_ >= 0) v = sh_ < 12 ? (m << sh_) : 0;
-      else v = (-sh_) >= 64 ? 0 : (m >> (-sh_));
     }
-    const int tk = (int)(k / OZ_BK), kk = (int)(k - (long long)tk * OZ_BK);
-    const int chunk = kk >> 3, j = kk & 7;
-    const long long within = (long long)rr * OZ_BK + ((chunk ^ (rr & 7)) << 3) + j;
-    for (int t = 1; t <= p.S; ++t) {
-      int d = (int)((v >> (7 * (p.S - t))) & 127ULL);
-      if (neg) d = -d;
-      const long long tile = ((long long)(t - 1) * p.T + tr) * p.KT + tk;
-      dst[tile * tile_elems + within] = __float2bfloat16_rn((float)d);
+    // one atomic per warp when the whole warp works on one row
+    const long long r0 = __shfl_sync(0xffffffffu, r, 0);
+    if (__all_sync(0xffffffffu, r == r0)) {
+      v = __reduce_max_sync(0xffffffffu, v);
+      if ((threadIdx.x & 31) == 0 && r0 >= 0 && v) atomicMax(eu + r0, v);
+    } else if (r >= 0 && v) {
+      atomicMax(eu + r, v);
     }
   }
+}
+
+// S digits of 7 bits of each element (sign and magnitude), bf16 encodings of
+// the magnitudes 0..127 from a shared table
+template <int S>
+__global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const OzPack p, const unsigned* eu, __nv_bfloat16* dst,
+                                                         int kfast, FastDiv fQ, FastDiv fR, unsigned W) {
+  __shared__ uint32_t bf[128];
+  if (threadIdx.x < 128) bf[threadIdx.x] = __float_as_uint((float)threadIdx.x) >> 16;  // exact for 0..127
+  __syncthreads();
+  const long long tile_elems = (long long)p.TR * OZ_BK;
+  constexpr int F = 7 * S;
+  const unsigned stride = gridDim.x * PACK_T;
+  for (unsigned i = blockIdx.x * PACK_T + threadIdx.x; i < W; i += stride) {
+    unsigned r, q;
+    pack_item(i, fQ, fR, kfast != 0, r, q);
+    long long x[8];
+    pack_load8(p, r, q, x);
+    const int e = r < (unsigned long long)p.R ? (int)eu[r] - (int)OZ_EBIAS : 0;
+    unsigned long long v[8];
+    unsigned neg = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      v[j] = 0;
+      const long long bits = x[j];
+      if ((bits << 1) != 0) {
+        if (bits < 0) neg |= 1u << j;
+        const int be = (int)((bits >> 52) & 0x7FF);
+        unsigned long long m = (unsigned long long)(bits & ((1LL << 52) - 1));
+        int E;
+        if (be) {
+          m |= 1ULL << 52;
+          E = be - 1075;
+        } else {
+          E = -1074;
+        }
+        const int sh_ = E + F - e;  // v = m 2^sh < 2^F
+        if (sh_ >= 0) v[j] = sh_ < 12 ? (m << sh_) : 0;
+        else v[j] = (-sh_) >= 64 ? 0 : (m >> (-sh_));
+      }
+    }
+    const unsigned tr = r / p.TR, rr = r - tr * p.TR;  // TR is 32, 64 or 128
+    const int tk = (int)(q >> 3), chunk = (int)(q & 7);
+    const long long within = (long long)rr * OZ_BK + ((chunk ^ (rr & 7)) << 3);
+#pragma unroll
+    for (int t = 1; t <= S; ++t) {
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        uint32_t pair = 0;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int j = 2 * h + u;
+          const uint32_t mag = (uint32_t)(v[j] >> (7 * (S - t))) & 127u;
+          const uint32_t sgn = (neg >> j & 1u) && mag ? 0x8000u : 0u;
+          pair |= (bf[mag] | sgn) << (16 * u);
+        }
+        w[h] = pair;
+      }
+      const long long tile = ((long long)(t - 1) * p.T + tr) * p.KT + tk;
+      *reinterpret_cast<uint4*>(dst + tile * tile_elems + within) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+inline int oz_pack_grid(long long n) {
+  long long b = (n + PACK_T - 1) / PACK_T;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)b;
+}
+
+// rows or k along the coalesced direction of the source (see the pack kernels)
+inline int pack_kfast(const OzPack& p) {
+  if (p.nK > 0 && p.sK[p.nK - 1] == 1) return 1;
+  if (p.nR > 0 && p.sR[p.nR - 1] == 1) return 0;
+  return 1;
 }
 
 inline int oz_grid(long long n) {
@@ -440,13 +633,11 @@ inline int oz_grid(long long n) {
   return (int)b;
 }
 
-int* oz_status_ptr() {
-  int* p = nullptr;
-  check_cuda(cudaGetSymbolAddress((void**)&p, g_oz_status), "cudaGetSymbolAddress (status)");
-  return p;
+size_t oz_smem_bytes(int S, int BN) {
+  const size_t tiles = (size_t)S * OZ_TILE_BYTES + (size_t)S * BN * OZ_BK * 2;
+  const size_t stage = (size_t)OZ_BM * (BN + 1) * sizeof(double);  // epilogue tile
+  return (tiles > stage ? tiles : stage) + 1024;
 }
-
-size_t oz_smem_bytes(int S, int BN) { return (size_t)S * OZ_TILE_BYTES + (size_t)S * BN * OZ_BK * 2 + 1024; }
 
 template <int BN>
 void oz_launch_bn(const OzArgs& a, int MT, int NT, cudaStream_t st) {
@@ -475,12 +666,18 @@ int ozaki_status(cudaStream_t st) {
   return v;
 }
 
+bool ozaki_supported(const GemmArgs& g) {
+  // packing indexes (padded rows) x (8-element k groups) with 32 bits
+  const long long big = g.M > g.N ? g.M : g.N;
+  const long long rows = (big + OZ_BM - 1) / OZ_BM * OZ_BM, groups = (g.K + OZ_BK - 1) / OZ_BK * (OZ_BK / 8);
+  return g.M < (1LL << 31) && g.N < (1LL << 31) && g.K < (1LL << 31) && rows * groups < (1LL << 32);
+}
+
 void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
   if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0) return;
   if (g0.nbatch != 1) throw std::runtime_error("split-precision contraction needs nbatch == 1");
   if (S < 1 || S > kOzakiMaxSlices) throw std::runtime_error("split-precision slices must be 1..7");
-  if (g0.M >= (1LL << 31) || g0.N >= (1LL << 31) || g0.K >= (1LL << 31))
-    throw std::runtime_error("split-precision contraction sizes must stay below 2^31");
+  if (!ozaki_supported(g0)) throw std::runtime_error("split-precision contraction too large for 32-bit packing");
   // orient so that the longer output side runs along the 128-row A tiles:
   // C^T = B^T A^T just exchanges the roles of the operands
   const bool swap = g0.N > g0.M;
@@ -497,6 +694,10 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
     }
     p.K = g0.K;
     p.S = S;
+    for (int d = 0; d < 4; ++d) {
+      p.fR[d] = make_fastdiv(d < nR ? (unsigned)eR[d] : 1u);
+      p.fK[d] = make_fastdiv(d < g0.nK ? (unsigned)g0.eK[d] : 1u);
+    }
   };
   long long M, N;
   if (!swap) {
@@ -530,7 +731,9 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
       a.cN[d] = g0.cM[d];
     }
   }
-  const int BN = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  int BN = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  // shared memory per CTA is capped at 227 KiB (static arrays take up to 4 KiB)
+  while (BN > 32 && oz_smem_bytes(S, BN) + 4096 > 227 * 1024) BN /= 2;
   const int MT = (int)((M + OZ_BM - 1) / OZ_BM), NT = (int)((N + BN - 1) / BN);
   const int KT = (int)((g0.K + OZ_BK - 1) / OZ_BK);
   pa.R = M;
@@ -563,11 +766,39 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
   if (splits > 1) part = ws.get((size_t)splits * MT * OZ_BM * NT * BN, capP);
   int* ea = (int*)bufE;
   int* fb = ea + (size_t)MT * OZ_BM;
-  int r = ws.begin(K_OZAKI_PACK, 0.0, 8.0 * (double)(M + N) * (double)g0.K * 2.0);
-  k_ozaki_pack<<<(unsigned)(MT * OZ_BM), PACK_T, 0, st>>>(pa, ea, (__nv_bfloat16*)bufA);
-  k_ozaki_pack<<<(unsigned)(NT * BN), PACK_T, 0, st>>>(pb, fb, (__nv_bfloat16*)bufB);
+  // algorithmic bytes: each operand element read twice (8 B each), S bf16 digits written
+  int r = ws.begin(K_OZAKI_PACK, 0.0, (16.0 + 2.0 * S) * (double)(M + N) * (double)g0.K);
+  if (r >= 0) {
+    ws.recs[r].m = M;
+    ws.recs[r].n = N;
+    ws.recs[r].k = g0.K;
+  }
+  check_cuda(cudaMemsetAsync(ea, 0, nE * sizeof(int), st), "cudaMemsetAsync (exponents)");
+  for (int o = 0; o < 2; ++o) {
+    const OzPack& p = o ? pb : pa;
+    unsigned* eu = (unsigned*)(o ? fb : ea);
+    __nv_bfloat16* dst = (__nv_bfloat16*)(o ? bufB : bufA);
+    const int kf = pack_kfast(p);
+    const long long rows = (long long)p.T * p.TR;
+    const long long q1 = (p.K + 7) / 8, q2 = (long long)p.KT * (OZ_BK / 8);
+    const FastDiv fr = make_fastdiv((unsigned)rows);
+    k_ozaki_rowexp<<<oz_pack_grid(rows * q1), PACK_T, 0, st>>>(p, eu, kf, make_fastdiv((unsigned)q1), fr,
+                                                                 (unsigned)(rows * q1));
+    const FastDiv f2 = make_fastdiv((unsigned)q2);
+    const unsigned w2 = (unsigned)(rows * q2);
+    const int g2 = oz_pack_grid(rows * q2);
+    switch (S) {
+      case 1: k_ozaki_digits<1><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
+      case 2: k_ozaki_digits<2><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
+      case 3: k_ozaki_digits<3><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
+      case 4: k_ozaki_digits<4><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
+      case 5: k_ozaki_digits<5><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
+      case 6: k_ozaki_digits<6><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
+      default: k_ozaki_digits<7><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
+    }
+  }
   ws.end(r);
-  ws.launches += 1;
+  ws.launches += 4;
   a.As = (const __nv_bfloat16*)bufA;
   a.Bs = (const __nv_bfloat16*)bufB;
   a.ea = ea;
@@ -584,9 +815,15 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
   a.splits = splits;
   a.ktper = ktper;
   a.part = part;
+  a.rowfast = (a.nM > 0 && a.nN > 0 && a.cM[a.nM - 1] < a.cN[a.nN - 1]) || (a.nN == 0 && a.nM > 0) ? 1 : 0;
   // executed tensor-core flops: digit pairs with t + u <= S + 1, padded tiles
   const double pairs = (double)S * (S + 1) / 2.0;
   r = ws.begin(kind, 2.0 * pairs * (double)MT * OZ_BM * (double)NT * BN * (double)KT * OZ_BK, 0.0);
+  if (r >= 0) {
+    ws.recs[r].m = M;
+    ws.recs[r].n = N;
+    ws.recs[r].k = g0.K;
+  }
   oz_launch_mma(a, MT, NT, BN, st);
   ws.end(r);
   if (splits > 1) ws.launches++;

@@ -28,5 +28,7 @@ const void* g_oz_status_alias();
 // C[m,n] += alpha * sum_k A[m,k] B[k,n] for the multi-index contraction g
 // (nbatch must be 1) with `slices` digits per operand.  Scratch comes from ws.
 void ozaki_gemm(Workspace& ws, const GemmArgs& g, int slices, int kind);
+// sizes the split-precision path can index (32-bit packing work items)
+bool ozaki_supported(const GemmArgs& g);
 
 }  // namespace dsrg
