@@ -101,31 +101,50 @@ void Workspace::prof_collect() {
   recs.clear();
 }
 
+namespace {
+// split-precision tensor-core path for every contraction with enough work
+// to pay for the operand slicing (about 40 us on the FP64 units); narrow
+// outputs use 32-column tiles, short ones split k over CTAs
+bool split_route(const Workspace& ws, const GemmArgs& g) {
+  return ws.slices > 0 && g.nbatch == 1 && g.K >= 32 && 2.0 * (double)g.M * (double)g.N * (double)g.K >= 5e7 &&
+         ozaki_supported(g);
+}
+
+// one flat launch over the output blocks of tab (npairs operand pairs)
+void run_gemm_flat(Workspace& ws, const GemmArgs& g, const FlatTable& tab, int npairs) {
+  const FlatPlan fp = gemm_flat_plan(g, tab.ngroups);
+  const size_t O = (size_t)(g.M * g.N * g.nbatch);
+  double* fpart = nullptr;
+  size_t fcap = 0;
+  if (fp.z > 1) fpart = ws.get((size_t)tab.ngroups * fp.z * O, fcap);
+  int r = ws.begin(K_GEMM, 2.0 * (double)g.M * (double)g.N * (double)g.K * (double)g.nbatch * npairs, 0.0);
+  if (r >= 0) {
+    ws.recs[r].m = g.M;
+    ws.recs[r].n = g.N;
+    ws.recs[r].k = g.K * g.nbatch * npairs;
+  }
+  launch_gemm_flat(g, fp, tab, fpart, ws.stream);
+  ws.end(r);
+  if (fp.z > 1) ws.launches++;
+  if (fpart) ws.put(fpart, fcap);
+}
+}  // namespace
+
 void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
   if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0 || g0.nbatch <= 0) return;
-  // split-precision tensor-core path for every contraction with enough work
-  // to pay for the operand slicing (about 40 us on the FP64 units); narrow
-  // outputs use 32-column tiles, short ones split k over CTAs
-  if (ws.slices > 0 && g0.nbatch == 1 && g0.K >= 32 && 2.0 * (double)g0.M * (double)g0.N * (double)g0.K >= 5e7 &&
-      ozaki_supported(g0)) {
+  if (split_route(ws, g0)) {
     ozaki_gemm(ws, g0, ws.slices, kind == K_GEMM ? (int)K_OZAKI_MMA : kind);
     return;
   }
   if (kind == K_GEMM && gemm_use_flat(g0)) {
-    const FlatPlan fp = gemm_flat_plan(g0);
-    double* fpart = nullptr;
-    size_t fcap = 0;
-    if (fp.z > 1) fpart = ws.get((size_t)fp.z * (size_t)(g0.M * g0.N * g0.nbatch), fcap);
-    int r = ws.begin(kind, 2.0 * (double)g0.M * (double)g0.N * (double)g0.K * (double)g0.nbatch, 0.0);
-    if (r >= 0) {
-      ws.recs[r].m = g0.M;
-      ws.recs[r].n = g0.N;
-      ws.recs[r].k = g0.K * g0.nbatch;
-    }
-    launch_gemm_flat(g0, fp, fpart, ws.stream);
-    ws.end(r);
-    if (fp.z > 1) ws.launches++;
-    if (fpart) ws.put(fpart, fcap);
+    FlatTable tab{};
+    tab.a[0] = g0.A;
+    tab.b[0] = g0.B;
+    tab.c[0] = g0.C;
+    tab.first[0] = 0;
+    tab.first[1] = 1;
+    tab.ngroups = 1;
+    run_gemm_flat(ws, g0, tab, 1);
     return;
   }
   GemmArgs g = g0;
@@ -376,15 +395,11 @@ bool contract(Workspace& ws, double alpha, const View& A, const char* la, const 
     if (l.iv.empty()) return false;
   if (L.size() > 16) throw std::runtime_error("too many labels");
   View a = restrict_view(A, la, L), b = restrict_view(B, lb, L), c = restrict_view(C.v, lc, L);
-  bool any = false;
-  for (int assign = 0; assign < (1 << L.size()); ++assign) {
-    int ba = spin_bits(a, la, L, assign), bb = spin_bits(b, lb, L, assign), bc = spin_bits(c, lc, L, assign);
-    if (!((a.mask >> ba) & 1) || !((b.mask >> bb) & 1)) continue;
-    GemmArgs g{};
-    g.A = a.p + spin_off(a, ba);
-    g.B = b.p + spin_off(b, bb);
-    g.C = c.p + spin_off(c, bc);
-    g.alpha = alpha;
+  // the geometry is the same for every spin assignment; only the block
+  // offsets differ
+  GemmArgs g{};
+  g.alpha = alpha;
+  {
     std::vector<Dim> M, N, K, Bt;
     for (auto& l : L) {
       int e = l.iv.len();
@@ -399,34 +414,74 @@ bool contract(Workspace& ws, double alpha, const View& A, const char* la, const 
     fill_group(N, g.nN, g.eN, g.bN, g.cN);
     fill_group(K, g.nK, g.eK, g.aK, g.bK);
     // batch labels need a C stride too
-    {
-      std::sort(Bt.begin(), Bt.end(), [](const Dim& x, const Dim& y) { return x.s1 > y.s1; });
-      if (Bt.size() > 4) throw std::runtime_error("too many batch labels");
-      g.nB = (int)Bt.size();
-      for (int i = 0; i < g.nB; ++i) {
-        g.eB[i] = Bt[i].e;
-        g.aB[i] = Bt[i].s1;
-        g.bB[i] = Bt[i].s2;
-      }
-      // C strides of batch labels, in the same order
-      int bi = 0;
-      std::vector<std::pair<long long, long long>> cb;
-      for (auto& l : L)
-        if (l.inA >= 0 && l.inB >= 0 && l.inC >= 0) cb.push_back({a.st[l.inA], c.st[l.inC]});
-      std::sort(cb.begin(), cb.end(), [](auto& x, auto& y) { return x.first > y.first; });
-      for (auto& x : cb) g.cB[bi++] = x.second;
+    std::sort(Bt.begin(), Bt.end(), [](const Dim& x, const Dim& y) { return x.s1 > y.s1; });
+    if (Bt.size() > 4) throw std::runtime_error("too many batch labels");
+    g.nB = (int)Bt.size();
+    for (int i = 0; i < g.nB; ++i) {
+      g.eB[i] = Bt[i].e;
+      g.aB[i] = Bt[i].s1;
+      g.bB[i] = Bt[i].s2;
     }
-    g.M = g.N = g.K = g.nbatch = 1;
-    for (int i = 0; i < g.nM; ++i) g.M *= g.eM[i];
-    for (int i = 0; i < g.nN; ++i) g.N *= g.eN[i];
-    for (int i = 0; i < g.nK; ++i) g.K *= g.eK[i];
-    for (int i = 0; i < g.nB; ++i) g.nbatch *= g.eB[i];
-    if (g.nbatch > 65535) throw std::runtime_error("batch too large");
-    run_gemm(ws, g);
-    C.v.mask |= 1ULL << bc;
-    any = true;
+    // C strides of batch labels, in the same order
+    int bi = 0;
+    std::vector<std::pair<long long, long long>> cb;
+    for (auto& l : L)
+      if (l.inA >= 0 && l.inB >= 0 && l.inC >= 0) cb.push_back({a.st[l.inA], c.st[l.inC]});
+    std::sort(cb.begin(), cb.end(), [](auto& x, auto& y) { return x.first > y.first; });
+    for (auto& x : cb) g.cB[bi++] = x.second;
   }
-  return any;
+  g.M = g.N = g.K = g.nbatch = 1;
+  for (int i = 0; i < g.nM; ++i) g.M *= g.eM[i];
+  for (int i = 0; i < g.nN; ++i) g.N *= g.eN[i];
+  for (int i = 0; i < g.nK; ++i) g.K *= g.eK[i];
+  for (int i = 0; i < g.nB; ++i) g.nbatch *= g.eB[i];
+  if (g.nbatch > 65535) throw std::runtime_error("batch too large");
+  struct Pair {
+    long long oa, ob, oc;
+  };
+  std::vector<Pair> pairs;
+  for (int assign = 0; assign < (1 << L.size()); ++assign) {
+    int ba = spin_bits(a, la, L, assign), bb = spin_bits(b, lb, L, assign), bc = spin_bits(c, lc, L, assign);
+    if (!((a.mask >> ba) & 1) || !((b.mask >> bb) & 1)) continue;
+    pairs.push_back({spin_off(a, ba), spin_off(b, bb), spin_off(c, bc)});
+    C.v.mask |= 1ULL << bc;
+  }
+  if (pairs.empty()) return false;
+  if (!split_route(ws, g) && gemm_use_flat(g)) {
+    // all spin blocks in flat launches: pairs that share an output block are
+    // summed inside one thread, so no two CTAs of a launch write the same C
+    std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& x, const Pair& y) { return x.oc < y.oc; });
+    FlatTable tab{};
+    int np = 0;
+    auto flush = [&]() {
+      if (tab.ngroups == 0) return;
+      tab.first[tab.ngroups] = np;
+      run_gemm_flat(ws, g, tab, np);
+      tab = FlatTable{};
+      np = 0;
+    };
+    for (size_t i = 0; i < pairs.size(); ++i) {
+      if (np == kFlatMaxPairs) flush();
+      const bool new_group = tab.ngroups == 0 || c.p + pairs[i].oc != tab.c[tab.ngroups - 1] || np == 0;
+      if (new_group) {
+        tab.c[tab.ngroups] = c.p + pairs[i].oc;
+        tab.first[tab.ngroups] = np;
+        ++tab.ngroups;
+      }
+      tab.a[np] = a.p + pairs[i].oa;
+      tab.b[np] = b.p + pairs[i].ob;
+      ++np;
+    }
+    flush();
+    return true;
+  }
+  for (auto& pr : pairs) {
+    g.A = a.p + pr.oa;
+    g.B = b.p + pr.ob;
+    g.C = c.p + pr.oc;
+    run_gemm(ws, g);
+  }
+  return true;
 }
 
 void axpy(Workspace& ws, double alpha, const View& A, const char* la, Tensor& C, const char* lc) {

@@ -302,8 +302,8 @@ __device__ __forceinline__ void flat_out(const GemmArgs& g, const FlatK& fk, lon
 }
 
 template <int WK>
-__global__ void __launch_bounds__(256) k_gemm_flat(const GemmArgs g, const FlatK fk, long long O, int mfast,
-                                                   long long len, double* part) {
+__global__ void __launch_bounds__(256) k_gemm_flat(const GemmArgs g, const FlatK fk, const FlatTable tab, long long O,
+                                                   int mfast, long long len, double* part) {
   constexpr int OG = 8 / WK;  // groups of 32 outputs per CTA
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int og = warp / WK, wk = warp - og * WK;
@@ -314,9 +314,8 @@ __global__ void __launch_bounds__(256) k_gemm_flat(const GemmArgs g, const FlatK
   double acc = 0.0;
   long long oA = 0, oB = 0, oC = 0;
   if (o < O) flat_out(g, fk, o, mfast, oA, oB, oC);
+  const int grp = blockIdx.z;
   if (o < O && klo < khi) {
-    const double* A = g.A + oA;
-    const double* B = g.B + oB;
     int i0, i1, i2, i3;
     long long ka, kb;
     {
@@ -356,30 +355,43 @@ __global__ void __launch_bounds__(256) k_gemm_flat(const GemmArgs g, const FlatK
         }
       }
     };
-    long long k = klo;
+    const int j0 = i0, j1 = i1, j2 = i2, j3 = i3;
+    const long long ka0 = ka, kb0 = kb;
     double acc1 = 0.0;
-    for (; k + 4 <= khi; k += 4) {
-      long long pa[4], pb[4];
+    // the block pairs of this output block, in table order
+    for (int pr = tab.first[grp]; pr < tab.first[grp + 1]; ++pr) {
+      const double* A = tab.a[pr] + oA;
+      const double* B = tab.b[pr] + oB;
+      i0 = j0;
+      i1 = j1;
+      i2 = j2;
+      i3 = j3;
+      ka = ka0;
+      kb = kb0;
+      long long k = klo;
+      for (; k + 4 <= khi; k += 4) {
+        long long pa[4], pb[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        pa[u] = ka;
-        pb[u] = kb;
+        for (int u = 0; u < 4; ++u) {
+          pa[u] = ka;
+          pb[u] = kb;
+          step();
+        }
+        double av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          av[u] = __ldg(A + pa[u]);
+          bv[u] = __ldg(B + pb[u]);
+        }
+        acc = fma(av[0], bv[0], acc);
+        acc1 = fma(av[1], bv[1], acc1);
+        acc = fma(av[2], bv[2], acc);
+        acc1 = fma(av[3], bv[3], acc1);
+      }
+      for (; k < khi; ++k) {
+        acc = fma(__ldg(A + ka), __ldg(B + kb), acc);
         step();
       }
-      double av[4], bv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        av[u] = __ldg(A + pa[u]);
-        bv[u] = __ldg(B + pb[u]);
-      }
-      acc = fma(av[0], bv[0], acc);
-      acc1 = fma(av[1], bv[1], acc1);
-      acc = fma(av[2], bv[2], acc);
-      acc1 = fma(av[3], bv[3], acc1);
-    }
-    for (; k < khi; ++k) {
-      acc = fma(__ldg(A + ka), __ldg(B + kb), acc);
-      step();
     }
     acc += acc1;
   }
@@ -391,20 +403,21 @@ __global__ void __launch_bounds__(256) k_gemm_flat(const GemmArgs g, const FlatK
       for (int w = 1; w < WK; ++w) acc += sh[warp + w][lane];
   }
   if (wk == 0 && o < O) {
-    if (gridDim.y > 1) part[(long long)blockIdx.y * O + o] = acc;
-    else g.C[oC] += g.alpha * acc;
+    if (gridDim.y > 1) part[((long long)grp * gridDim.y + blockIdx.y) * O + o] = acc;
+    else tab.c[grp][oC] += g.alpha * acc;
   }
 }
 
-// C[o] += alpha * sum_z part[z][o], z in increasing order
-__global__ void k_gemm_flat_reduce(const GemmArgs g, const FlatK fk, long long O, int mfast, int Z,
-                                   const double* part) {
+// C_grp[o] += alpha * sum_z part[grp][z][o], z in increasing order (grp = blockIdx.y)
+__global__ void k_gemm_flat_reduce(const GemmArgs g, const FlatK fk, const FlatTable tab, long long O, int mfast,
+                                   int Z, const double* part) {
+  const int grp = blockIdx.y;
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < O; o += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int z = 0; z < Z; ++z) s += part[(long long)z * O + o];
+    for (int z = 0; z < Z; ++z) s += part[((long long)grp * Z + z) * O + o];
     long long oA, oB, oC;
     flat_out(g, fk, o, mfast, oA, oB, oC);
-    g.C[oC] += g.alpha * s;
+    tab.c[grp][oC] += g.alpha * s;
   }
 }
 
@@ -726,9 +739,9 @@ bool gemm_use_flat(const GemmArgs& g) {
   return !(g.M >= 64 && g.N >= 64 && g.K > 64 && tiles >= 2 * 152);
 }
 
-FlatPlan gemm_flat_plan(const GemmArgs& g) {
+FlatPlan gemm_flat_plan(const GemmArgs& g, int groups) {
   FlatPlan p{};
-  const long long O = g.M * g.N * g.nbatch;
+  const long long O = g.M * g.N * g.nbatch * (groups > 1 ? groups : 1);
   // about 32 resident warps per SM: enough FMAs in flight to cover latency
   const long long target = 152LL * 1024;
   long long chunks = (target + O - 1) / O;
@@ -747,9 +760,9 @@ FlatPlan gemm_flat_plan(const GemmArgs& g) {
   return p;
 }
 
-void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, double* part, cudaStream_t st) {
+void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, const FlatTable& tab, double* part, cudaStream_t st) {
   const long long O = g.M * g.N * g.nbatch;
-  if (O <= 0 || g.K <= 0) return;
+  if (O <= 0 || g.K <= 0 || tab.ngroups <= 0) return;
   FlatK fk{};
   const int pad = 4 - g.nK;
   for (int d = 0; d < 4; ++d) {
@@ -771,14 +784,17 @@ void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, double* part, cudaSt
   fk.fM = make_fastdiv((unsigned)g.M);
   fk.fN = make_fastdiv((unsigned)g.N);
   const long long per_cta = 32LL * (8 / p.wk);
-  dim3 grid((unsigned)((O + per_cta - 1) / per_cta), (unsigned)p.z);
+  dim3 grid((unsigned)((O + per_cta - 1) / per_cta), (unsigned)p.z, (unsigned)tab.ngroups);
   switch (p.wk) {
-    case 8: k_gemm_flat<8><<<grid, 256, 0, st>>>(g, fk, O, p.mfast, p.len, part); break;
-    case 4: k_gemm_flat<4><<<grid, 256, 0, st>>>(g, fk, O, p.mfast, p.len, part); break;
-    case 2: k_gemm_flat<2><<<grid, 256, 0, st>>>(g, fk, O, p.mfast, p.len, part); break;
-    default: k_gemm_flat<1><<<grid, 256, 0, st>>>(g, fk, O, p.mfast, p.len, part); break;
+    case 8: k_gemm_flat<8><<<grid, 256, 0, st>>>(g, fk, tab, O, p.mfast, p.len, part); break;
+    case 4: k_gemm_flat<4><<<grid, 256, 0, st>>>(g, fk, tab, O, p.mfast, p.len, part); break;
+    case 2: k_gemm_flat<2><<<grid, 256, 0, st>>>(g, fk, tab, O, p.mfast, p.len, part); break;
+    default: k_gemm_flat<1><<<grid, 256, 0, st>>>(g, fk, tab, O, p.mfast, p.len, part); break;
   }
-  if (p.z > 1) k_gemm_flat_reduce<<<grid_for(O, 256), 256, 0, st>>>(g, fk, O, p.mfast, p.z, part);
+  if (p.z > 1) {
+    const dim3 rg((unsigned)grid_for(O, 256, (152 * 16 + tab.ngroups - 1) / tab.ngroups), (unsigned)tab.ngroups);
+    k_gemm_flat_reduce<<<rg, 256, 0, st>>>(g, fk, tab, O, p.mfast, p.z, part);
+  }
 }
 
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind) {

@@ -105,9 +105,23 @@ struct FlatPlan {
   long long len;  // k per chunk
   int mfast;      // lanes along m (1) or n (0)
 };
+// Output blocks of one flat launch: block j accumulates the products of the
+// operand pairs first[j] .. first[j+1]-1 (same geometry as the GemmArgs,
+// whose A, B, C pointers are ignored) into c[j].  Distinct c[j] only.
+constexpr int kFlatMaxPairs = 64;
+struct FlatTable {
+  const double* a[kFlatMaxPairs];
+  const double* b[kFlatMaxPairs];
+  double* c[kFlatMaxPairs];
+  int first[kFlatMaxPairs + 1];
+  int ngroups;
+};
 bool gemm_use_flat(const GemmArgs& g);
-FlatPlan gemm_flat_plan(const GemmArgs& g);
-void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, double* part, cudaStream_t st);
+// plan for `groups` output blocks (the chunking along k covers the GPU with
+// all of them together)
+FlatPlan gemm_flat_plan(const GemmArgs& g, int groups = 1);
+// part needs groups * z * M*N*nbatch doubles when the plan has z > 1
+void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, const FlatTable& tab, double* part, cudaStream_t st);
 // kind 0: generic contraction, 1: DF build of (pr|qs), 2: ladder contraction
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind = 0);
 void launch_fill(double* p, long long n, double v, cudaStream_t st);
