@@ -6,6 +6,8 @@
 
 #include "ozaki.cuh"
 
+#include <algorithm>
+
 namespace dsrg {
 namespace {
 
@@ -147,6 +149,31 @@ __device__ __forceinline__ long long c_offset(long long lin, int nd, const int* 
     lin = q;
   }
   return o;
+}
+
+// paired FP32 arithmetic on two floats held in one 64-bit register
+__device__ __forceinline__ uint64_t f2_pack(uint32_t a, uint32_t b) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, uint32_t& a, uint32_t& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(a), "=r"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
 }
 
 // (double)f * 2^k assembled from the bit pattern of the float f (sign,
@@ -300,6 +327,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
       }
       // fold level c: (hi, lo) += acc * 2^(-7c), two-sum in FP32
       const float scale = exp2f(-7.0f * (float)c);
+      const uint64_t sc2 = f2_pack(__float_as_uint(scale), __float_as_uint(scale));
       const uint32_t src = (uint32_t)((c & 1) * BN);
 #pragma unroll 1
       for (int j = 0; j < nchunk; ++j) {
@@ -309,18 +337,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
         tmem_ld32(tm + lane_off + HI + cc, hi);
         tmem_ld32(tm + lane_off + LO + cc, lo);
         tmem_wait_ld();
+        // two columns per instruction (paired FP32, same IEEE rounding)
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          float x = __uint_as_float(acc[q]) * scale;
-          float h = __uint_as_float(hi[q]);
-          float s_ = h + x;
-          float bp = s_ - h;
-          float err = (h - (s_ - bp)) + (x - bp);
-          float l = __uint_as_float(lo[q]) + err;
-          float s2 = s_ + l;
-          l = l - (s2 - s_);
-          hi[q] = __float_as_uint(s2);
-          lo[q] = __float_as_uint(l);
+        for (int q = 0; q < 32; q += 2) {
+          const uint64_t x = f2_mul(f2_pack(acc[q], acc[q + 1]), sc2);
+          const uint64_t h = f2_pack(hi[q], hi[q + 1]);
+          const uint64_t s_ = f2_add(h, x);
+          const uint64_t bp = f2_sub(s_, h);
+          const uint64_t err = f2_add(f2_sub(h, f2_sub(s_, bp)), f2_sub(x, bp));
+          uint64_t l = f2_add(f2_pack(lo[q], lo[q + 1]), err);
+          const uint64_t s2 = f2_add(s_, l);
+          l = f2_sub(l, f2_sub(s2, s_));
+          f2_unpack(s2, hi[q], hi[q + 1]);
+          f2_unpack(l, lo[q], lo[q + 1]);
         }
         tmem_st32(tm + lane_off + HI + cc, hi);
         tmem_st32(tm + lane_off + LO + cc, lo);
@@ -517,8 +546,23 @@ __device__ __forceinline__ void pack_load8(const OzPack& p, unsigned r, unsigned
   }
 }
 
-__global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const OzPack p, unsigned* eu, int kfast, FastDiv fQ,
-                                                         FastDiv fR, unsigned W) {
+// Both operands of a product in one launch: blockIdx.y selects A (0) or B (1).
+struct PackPass {
+  OzPack p[2];
+  unsigned* eu[2];
+  __nv_bfloat16* dst[2];
+  int kfast[2];
+  FastDiv fQ[2], fR[2];
+  unsigned W[2];
+};
+
+__global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const PackPass pp) {
+  const int o = blockIdx.y;
+  const OzPack& p = pp.p[o];
+  unsigned* eu = pp.eu[o];
+  const int kfast = pp.kfast[o];
+  const FastDiv fQ = pp.fQ[o], fR = pp.fR[o];
+  const unsigned W = pp.W[o];
   const unsigned stride = gridDim.x * PACK_T;
   for (unsigned base = blockIdx.x * PACK_T; base < W; base += stride) {
     const unsigned i = base + threadIdx.x;
@@ -552,8 +596,14 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const OzPack p, unsigne
 // S digits of 7 bits of each element (sign and magnitude), bf16 encodings of
 // the magnitudes 0..127 from a shared table
 template <int S>
-__global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const OzPack p, const unsigned* eu, __nv_bfloat16* dst,
-                                                         int kfast, FastDiv fQ, FastDiv fR, unsigned W) {
+__global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
+  const int o = blockIdx.y;
+  const OzPack& p = pp.p[o];
+  const unsigned* eu = pp.eu[o];
+  __nv_bfloat16* dst = pp.dst[o];
+  const int kfast = pp.kfast[o];
+  const FastDiv fQ = pp.fQ[o], fR = pp.fR[o];
+  const unsigned W = pp.W[o];
   __shared__ uint32_t bf[128];
   if (threadIdx.x < 128) bf[threadIdx.x] = __float_as_uint((float)threadIdx.x) >> 16;  // exact for 0..127
   __syncthreads();
@@ -774,31 +824,38 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
     ws.recs[r].k = g0.K;
   }
   check_cuda(cudaMemsetAsync(ea, 0, nE * sizeof(int), st), "cudaMemsetAsync (exponents)");
+  PackPass pp{};
+  long long w1max = 1, w2max = 1;
+  PackPass pd{};
   for (int o = 0; o < 2; ++o) {
     const OzPack& p = o ? pb : pa;
-    unsigned* eu = (unsigned*)(o ? fb : ea);
-    __nv_bfloat16* dst = (__nv_bfloat16*)(o ? bufB : bufA);
-    const int kf = pack_kfast(p);
     const long long rows = (long long)p.T * p.TR;
     const long long q1 = (p.K + 7) / 8, q2 = (long long)p.KT * (OZ_BK / 8);
-    const FastDiv fr = make_fastdiv((unsigned)rows);
-    k_ozaki_rowexp<<<oz_pack_grid(rows * q1), PACK_T, 0, st>>>(p, eu, kf, make_fastdiv((unsigned)q1), fr,
-                                                                 (unsigned)(rows * q1));
-    const FastDiv f2 = make_fastdiv((unsigned)q2);
-    const unsigned w2 = (unsigned)(rows * q2);
-    const int g2 = oz_pack_grid(rows * q2);
-    switch (S) {
-      case 1: k_ozaki_digits<1><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
-      case 2: k_ozaki_digits<2><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
-      case 3: k_ozaki_digits<3><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
-      case 4: k_ozaki_digits<4><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
-      case 5: k_ozaki_digits<5><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
-      case 6: k_ozaki_digits<6><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
-      default: k_ozaki_digits<7><<<g2, PACK_T, 0, st>>>(p, eu, dst, kf, f2, fr, w2); break;
-    }
+    pp.p[o] = pd.p[o] = p;
+    pp.eu[o] = pd.eu[o] = (unsigned*)(o ? fb : ea);
+    pp.dst[o] = pd.dst[o] = (__nv_bfloat16*)(o ? bufB : bufA);
+    pp.kfast[o] = pd.kfast[o] = pack_kfast(p);
+    pp.fR[o] = pd.fR[o] = make_fastdiv((unsigned)rows);
+    pp.fQ[o] = make_fastdiv((unsigned)q1);
+    pd.fQ[o] = make_fastdiv((unsigned)q2);
+    pp.W[o] = (unsigned)(rows * q1);
+    pd.W[o] = (unsigned)(rows * q2);
+    w1max = std::max(w1max, rows * q1);
+    w2max = std::max(w2max, rows * q2);
+  }
+  k_ozaki_rowexp<<<dim3((unsigned)oz_pack_grid(w1max), 2), PACK_T, 0, st>>>(pp);
+  const dim3 g2((unsigned)oz_pack_grid(w2max), 2);
+  switch (S) {
+    case 1: k_ozaki_digits<1><<<g2, PACK_T, 0, st>>>(pd); break;
+    case 2: k_ozaki_digits<2><<<g2, PACK_T, 0, st>>>(pd); break;
+    case 3: k_ozaki_digits<3><<<g2, PACK_T, 0, st>>>(pd); break;
+    case 4: k_ozaki_digits<4><<<g2, PACK_T, 0, st>>>(pd); break;
+    case 5: k_ozaki_digits<5><<<g2, PACK_T, 0, st>>>(pd); break;
+    case 6: k_ozaki_digits<6><<<g2, PACK_T, 0, st>>>(pd); break;
+    default: k_ozaki_digits<7><<<g2, PACK_T, 0, st>>>(pd); break;
   }
   ws.end(r);
-  ws.launches += 4;
+  ws.launches += 2;  // memset + two pack passes (begin() counted one)
   a.As = (const __nv_bfloat16*)bufA;
   a.Bs = (const __nv_bfloat16*)bufB;
   a.ea = ea;
