@@ -205,7 +205,9 @@ def alg_flops(inst):
 
 def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, clocks=None):
     """Warm up, then time `steps` PT3 energies (CUDA events on the library's
-    stream, L2 flushed before each step, per-kernel events inside)."""
+    stream around each step, L2 flushed before each step), then run one more
+    energy with per-kernel events for the kernel breakdown (kept out of the
+    timed steps, whose launches it would slow down)."""
     prec = g.DSRG_PREC_SPLIT if precision == "split" else g.DSRG_PREC_FP64
     h = g.Dsrg(dev, stream=stream.cuda_stream, precision=prec, slices=slices if precision == "split" else 0)
     energies = None
@@ -214,7 +216,6 @@ def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, c
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
-    h.profile(True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     launches = 0
@@ -228,9 +229,16 @@ def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, c
             ends[k].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
+    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    # one profiled energy: per-kernel device time, launches and flops of a step
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    torch.cuda.synchronize()
+    h.profile(True)
+    h.pt3()
+    torch.cuda.synchronize()
     stats = h.profile_stats()
     h.profile(False)
-    ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     return h, ms, energies, stats, launches, clk
 
 
@@ -256,9 +264,11 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     other = "fp64" if args.precision == "split" else "split"
     # comparison path first (untimed for the headline), then the headline path
-    h2, ms2, e_other, stats2, _, _ = _time_path(g, torch, dev, stream, flush, max(1, min(args.steps, 3)),
-                                                args.warmup, other, args.slices)
-    h2.close()
+    ms2 = e_other = None
+    if not args.no_comparison:
+        h2, ms2, e_other, stats2, _, _ = _time_path(g, torch, dev, stream, flush, max(1, min(args.steps, 3)),
+                                                    args.warmup, other, args.slices)
+        h2.close()
     if dist:
         dist.barrier()
     h, ms, energies, stats, launches, clocks = _time_path(g, torch, dev, stream, flush, args.steps, args.warmup,
@@ -293,14 +303,16 @@ def run_ours(args, rank, world, local_rank):
         d2h = g.dsrg_last_d2h_bytes(h.h) + 32
     e2e_value = world * 1000.0 / statistics.median(e2e_ms)
     h.close()
-    # ---- roofline of the dominant kernel (by device time)
+    # ---- roofline of the dominant kernel (by device time in the profiled energy)
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
     af = alg_flops(inst)
-    steps = args.steps
+    step_s = total_s / args.steps
     if dom_name == "k_gemm<1>":
-        alg, note = af["build"] * steps, "Q p^2 (p^2+1) per energy ((pr|qs) build, pair-swap symmetry)"
+        alg, note = af["build"], "Q p^2 (p^2+1) per energy ((pr|qs) build, pair-swap symmetry)"
     elif dom_name == "k_gemm<2>":
-        alg, note = af["ladder"] * steps, "h (h+1) p^4 per energy (ladder, i <= j)"
+        alg, note = af["ladder"], "h (h+1) p^4 per energy (ladder, i <= j)"
+    elif dom_name == "k_ozaki_mma":
+        alg, note = dom["flops"], "executed bf16 flops: 2 x 128-row x tile-width x 64-k tiles x S(S+1)/2 digit pairs"
     else:
         alg, note = dom["flops"], "2 M N K summed over the kernel's contractions"
     tensor_kernel = dom_name == "k_ozaki_mma"
@@ -310,20 +322,29 @@ def run_ours(args, rank, world, local_rank):
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "of measured bf16 burst" if tensor_kernel else
                 "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz",
-                "algorithmic": note, "launches_per_step": dom["launches"] / steps,
+                "algorithmic": note, "launches_per_step": dom["launches"],
                 "avg_launch_ms": dom["ms"] / max(1, dom["launches"]),
-                "share_of_step": (dom["ms"] / 1000.0) / max(total_s, 1e-30)}
+                "share_of_step": (dom["ms"] / 1000.0) / max(step_s, 1e-30)}
     tensor = stats.get("k_ozaki_mma", {"launches": 0, "ms": 0.0, "flops": 0.0})
     roof_tensor = None
-    if tensor["launches"]:
+    if tensor["launches"] and dom_name != "k_ozaki_mma":
         executed = tensor["flops"] / (tensor["ms"] / 1000.0) / 1e12
         roof_tensor = {"kernel": "k_ozaki_mma", "bound": "tensor", "achieved": executed, "peak": MEASURED_BF16,
                        "unit": "TFLOP/s", "frac": executed / MEASURED_BF16,
                        "note": "executed bf16 flops (digit-slice pairs and tile padding included) per device time",
-                       "launches_per_step": tensor["launches"] / steps,
-                       "share_of_step": (tensor["ms"] / 1000.0) / max(total_s, 1e-30)}
+                       "launches_per_step": tensor["launches"],
+                       "share_of_step": (tensor["ms"] / 1000.0) / max(step_s, 1e-30)}
+    fp64k = stats.get("k_gemm<0>", {"launches": 0, "ms": 0.0, "flops": 0.0})
+    roof_fp64 = None
+    if fp64k["launches"] and dom_name != "k_gemm<0>":
+        a64 = fp64k["flops"] / (fp64k["ms"] / 1000.0) / 1e12
+        roof_fp64 = {"kernel": "k_gemm<0>", "bound": "alu", "achieved": a64, "peak": FP64_ALU_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": a64 / FP64_ALU_PEAK_TFLOPS,
+                     "note": "2 M N K of the FP64 contractions per device time",
+                     "launches_per_step": fp64k["launches"],
+                     "share_of_step": (fp64k["ms"] / 1000.0) / max(step_s, 1e-30)}
     eff_tflops = (af["ladder"] + af["build"]) * value / 1e12
-    err = {k: energies[k] - e_other[k] for k in ("e2", "e3a", "e3b", "e3")}
+    err = {k: energies[k] - e_other[k] for k in ("e2", "e3a", "e3b", "e3")} if e_other else None
     line = {
         "metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -332,13 +353,15 @@ def run_ours(args, rank, world, local_rank):
         "config": dict(config_dict(inst, args.precision), slices=args.slices if args.precision == "split" else None),
         "effective_tflops_ladder_build": eff_tflops,
         "energies": energies,
-        "comparison": {"precision": other, "ms_per_step": statistics.median(ms2), "value": 1000.0 / statistics.median(ms2),
-                       "energies": e_other, "headline_minus_comparison_Eh": err},
+        "comparison": None if ms2 is None else
+        {"precision": other, "ms_per_step": statistics.median(ms2), "value": 1000.0 / statistics.median(ms2),
+         "energies": e_other, "headline_minus_comparison_Eh": err},
         "clocks": clocks,
         "gpu_launches": launches,
         "roofline": roofline,
         "roofline_tensor": roof_tensor,
-        "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items() if v["launches"]},
+        "roofline_fp64": roof_fp64,
+        "kernels_per_step": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items() if v["launches"]},
         "e2e": {"value": e2e_value, "unit": "energies/s", "h2d_bytes_per_step": input_bytes(inst),
                 "d2h_bytes_per_step": d2h},
     }
@@ -365,6 +388,8 @@ def main(argv=None):
     ap.add_argument("--precision", choices=("split", "fp64"), default="split",
                     help="headline path; the other is timed alongside for comparison")
     ap.add_argument("--slices", type=int, default=6)
+    ap.add_argument("--no-comparison", action="store_true",
+                    help="skip timing the other precision (quick runs, profiler launch lists)")
     args = ap.parse_args(argv)
     rank, world, local_rank = rank_env()
     if args.impl == "reference":

@@ -74,6 +74,16 @@ void load_inputs(dsrg::Handle& h, const dsrg_inputs* in) {
     h.eta = make_tensor(h.ws, 2, pp, false);
     launch_build_gamma_eta(h.nc, na, h.nv, h.blk[0], h.blk[1], h.gam.v.p, h.eta.v.p, st);
     h.gam.v.mask = h.eta.v.mask = conserving_mask(2);
+    Iv aa[2] = {h.A, h.A};
+    h.gam_dI = make_tensor(h.ws, 2, aa, true);
+    h.eta_dI = make_tensor(h.ws, 2, aa, true);
+    if (na > 0) {
+      axpy(h.ws, 1.0, h.gam.v.sub(aa), "xy", h.gam_dI, "xy");
+      axpy(h.ws, 1.0, h.eta.v.sub(aa), "xy", h.eta_dI, "xy");
+      launch_add_diagonal(h.gam_dI.v.p, 2 * na, -1.0, st);
+      launch_add_diagonal(h.eta_dI.v.p, 2 * na, -1.0, st);
+    }
+    h.gam_dI.v.mask = h.eta_dI.v.mask = conserving_mask(2);
   }
   {
     Iv a4[4] = {h.A, h.A, h.A, h.A}, a6[6] = {h.A, h.A, h.A, h.A, h.A, h.A};

@@ -120,37 +120,86 @@ void build_v(Handle& h, unsigned classes, Sym2& V) {
 // or eta (particle range).  Both are the identity outside the active block
 // (gamma on core, eta on virtual), so the product is a copy there and a
 // small contraction with the active block.
+// Active rows of a dressing: out[.., z, ..] += sum_x Ma[z, x] X[.., x, ..]
+// over the slot's active orbitals x, z (Ma an [A, A] view).
+static void dress_active(Handle& h, const View& X, int slot, const View& Ma, Tensor& out) {
+  const int r = X.rank;
+  char lx[8], lo[8], lm[3];
+  for (int k = 0; k < r; ++k) lx[k] = lo[k] = "abcdef"[k];
+  lx[r] = lo[r] = 0;
+  lo[slot] = 'z';
+  lm[0] = 'z';
+  lm[1] = lx[slot];
+  lm[2] = 0;
+  contract(h.ws, 1.0, Ma, lm, X, lx, out, lo);
+}
+
+// (M - 1) on the active block for M = gamma or eta, else nullptr
+static const Tensor* dress_delta(const Handle& h, const Tensor& M) {
+  if (&M == &h.gam) return &h.gam_dI;
+  if (&M == &h.eta) return &h.eta_dI;
+  return nullptr;
+}
+
 Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M) {
+  ProfTag tag_(h.ws, "dress");
   const int r = X.v.rank;
   Iv ivs[kMaxRank];
   for (int k = 0; k < r; ++k) ivs[k] = X.v.iv[k];
   ivs[slot] = isect(M.v.iv[0], X.v.iv[slot]);
-  Tensor out = make_tensor(h.ws, r, ivs, true);
-  if (ivs[slot].empty()) return out;
-  char lx[8], lo[8], lm[3];
-  for (int k = 0; k < r; ++k) lx[k] = lo[k] = "abcdef"[k];
-  lx[r] = lo[r] = 0;
-  // identity part: the slot's orbitals outside the active space
   const Iv& sl = ivs[slot];
+  const bool active = h.na > 0 && !isect(sl, h.A).empty();
+  const Tensor* dM = dress_delta(h, M);
+  if (dM && !sl.empty() && sl.lo == X.v.iv[slot].lo && sl.hi == X.v.iv[slot].hi && X.n > 0) {
+    // same layout as X: a copy of X, plus (M - 1) X on the active rows
+    Tensor out = make_tensor(h.ws, r, ivs, false);
+    check_cuda(cudaMemcpyAsync(out.v.p, X.v.p, X.n * sizeof(double), cudaMemcpyDeviceToDevice, h.ws.stream),
+               "cudaMemcpyAsync (dress)");
+    out.v.mask = X.v.mask;
+    if (active) dress_active(h, X.v, slot, dM->v, out);
+    return out;
+  }
+  Tensor out = make_tensor(h.ws, r, ivs, true);
+  if (sl.empty()) return out;
+  char lx[8];
+  for (int k = 0; k < r; ++k) lx[k] = "abcdef"[k];
+  lx[r] = 0;
+  // identity part: the slot's orbitals outside the active space
   Iv parts[2] = {isect(sl, Iv{sl.lo, h.A.lo}), isect(sl, Iv{h.A.hi, sl.hi})};
   for (const Iv& part : parts) {
     if (part.empty()) continue;
     Iv sub[kMaxRank];
     for (int k = 0; k < r; ++k) sub[k] = ivs[k];
     sub[slot] = part;
-    View xv = X.v.sub(sub);
-    axpy(h.ws, 1.0, xv, lx, out, lx);
+    axpy(h.ws, 1.0, X.v.sub(sub), lx, out, lx);
   }
-  // active block
-  if (h.na > 0 && !isect(sl, h.A).empty()) {
+  if (active) {
     const Iv aa[2] = {h.A, h.A};
-    lo[slot] = 'z';
-    lm[0] = 'z';
-    lm[1] = lx[slot];
-    lm[2] = 0;
-    contract(h.ws, 1.0, M.v.sub(aa), lm, X.v, lx, out, lo);
+    dress_active(h, X.v, slot, M.v.sub(aa), out);
   }
   return out;
+}
+
+// In place on a temporary: (M - 1) X of the active rows goes through a
+// small tensor and is added back.
+Tensor dress(Handle& h, Tensor&& X, int slot, const Tensor& M) {
+  ProfTag tag_(h.ws, "dress-inplace");
+  const int r = X.v.rank;
+  const Iv sl = isect(M.v.iv[0], X.v.iv[slot]);
+  const Tensor* dM = dress_delta(h, M);
+  if (!dM || sl.lo != X.v.iv[slot].lo || sl.hi != X.v.iv[slot].hi || X.n == 0)
+    return dress(h, static_cast<const Tensor&>(X), slot, M);
+  if (h.na == 0 || isect(sl, h.A).empty()) return std::move(X);
+  Iv ivs[kMaxRank];
+  for (int k = 0; k < r; ++k) ivs[k] = X.v.iv[k];
+  ivs[slot] = isect(sl, h.A);
+  Tensor act = make_tensor(h.ws, r, ivs, true);
+  dress_active(h, X.v, slot, dM->v, act);
+  char lx[8];
+  for (int k = 0; k < r; ++k) lx[k] = "abcdef"[k];
+  lx[r] = 0;
+  axpy(h.ws, 1.0, act.v, lx, X, lx);
+  return std::move(X);
 }
 
 // ---------------------------------------------------------------------------
@@ -172,6 +221,7 @@ static Tensor gamma_source(Handle& h, const Tensor& T2) {
 }
 
 void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tensor& T2, Tensor& W1, Tensor& W2) {
+  ProfTag tag_(h.ws, "amplitudes");
   T2 = mk(h, {h.P, h.P, h.H, h.H}, false);
   W2 = mk(h, {h.P, h.P, h.H, h.H}, false);
   {
@@ -198,6 +248,7 @@ void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tenso
 // a spin-free T2 (first order, Eq. T2_1st); the spin blocks of
 // 1/2 sum_rs <pq||rs> T2[r,s,i,j] follow from L (Eq. scaling_problem).
 void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
+  ProfTag tag_(h.ws, "ladder");
   const int p = h.na + h.nv, hh = h.nc + h.na;
   if (p == 0 || hh == 0) return;
   const View& tv = T2.v;
@@ -272,6 +323,7 @@ static Op1Pieces op1_pieces(Handle& h, double c_f, const Tensor* W1, double c_w)
 void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
                 Tensor& C2, bool df, const Op1Pieces* X1p) {
   Workspace& ws = h.ws;
+  ProfTag tag_(ws, "commutator");
   const Tensor& g = h.gam;
   const Tensor& e = h.eta;
   const Tensor& L2 = h.L2;
@@ -404,6 +456,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   // X2 is taken piece by piece (V, then W and its Hermitian image on their
   // own boxes) so that no work is spent where a piece vanishes.
   {
+    ProfTag ring_tag(ws, "ring");
     Iv xi = exc ? P : H, wi = exc ? H : P;
     Iv want[4] = {xi, H, P, wi};
     // y and u must land in C2's slots as well as in T2's
@@ -445,22 +498,24 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
 // excitation blocks of [X, T - T^+] = [X, T] + [X, T]^+ (X Hermitian)
 void commutator_A(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& O1,
                   Tensor& O2, bool df, const Op1Pieces* X1p) {
-  Tensor C1e = mk(h, {h.P, h.H}), C1d = mk(h, {h.H, h.P});
-  Tensor C2e = mk(h, {h.P, h.P, h.H, h.H}), C2d = mk(h, {h.H, h.H, h.P, h.P});
-  commutator(h, X1, X2, T1, T2, C1e, C2e, df, X1p);
-  commutator(h, X1, X2, T1, T2, C1d, C2d, df, X1p);
   O1 = mk(h, {h.P, h.H});
   O2 = mk(h, {h.P, h.P, h.H, h.H});
-  axpy(h.ws, 1.0, C1e.v, "ai", O1, "ai");
+  // excitation blocks straight into O1, O2; the de-excitation blocks [H H P P]
+  // land in O2 through a slot-permuted alias (the commutator only accumulates)
+  commutator(h, X1, X2, T1, T2, O1, O2, df, X1p);
+  const int perm[4] = {2, 3, 0, 1};
+  Tensor C1d = mk(h, {h.H, h.P});
+  Tensor C2d = alias_permuted(O2, perm);
+  commutator(h, X1, X2, T1, T2, C1d, C2d, df, X1p);
+  merge_alias_mask(O2, C2d, perm);
   axpy(h.ws, 1.0, C1d.v, "ia", O1, "ai");
-  axpy(h.ws, 1.0, C2e.v, "abij", O2, "abij");
-  axpy(h.ws, 1.0, C2d.v, "ijab", O2, "abij");
 }
 
 // ---------------------------------------------------------------------------
 // scalar <[X, T]>: only the X1[H,P] and X2[H,H,P,P] elements enter
 // ---------------------------------------------------------------------------
 void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2) {
+  ProfTag tag_(h.ws, "scalar");
   Workspace& ws = h.ws;
   const Tensor& g = h.gam;
   const Tensor& e = h.eta;
@@ -570,6 +625,7 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   const Iv& H = h.H;
   const Iv& P = h.P;
   // first-order amplitudes from the non-diagonal part of H(1)
+  ws.tag = "first-order";
   Tensor F1ph = mk(h, {P, H});
   if (h.has_f1) axpy(ws, 1.0, h.F1.v, "ai", F1ph, "ai");
   Tensor Vph;
@@ -582,7 +638,9 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   Vph.release();
   // Htilde(1) = 2 H(1) + [H(0), A(1)] (Eq. Hbar_1st); V on the classes the terms need
   Sym2 V;
+  ws.tag = "build-v";
   build_v(h, pt3 ? 0x1fu : (1u << 2), V);
+  ws.tag = "E2";
   Tensor Xs1 = build_x1(h, 2.0, &W1, 1.0);
   Op2 Xs2{&V, 2.0, &W2, 1.0};
   int r0 = ws.nresults;
@@ -594,11 +652,13 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   if (!pt3) {
     *e3a = *e3b = 0.0;
     h.launches = ws.launches;
+    ws.tag = "";
     return;
   }
   const Tensor& t1 = h.T1;
   const Tensor& t2 = h.T2;
   // O = 1/2 [Htilde(1), A(1)]_{1,2} = [H(1) + W/2, A(1)]_{1,2}
+  ws.tag = "O";
   Tensor O1, O2;
   {
     Tensor X1 = build_x1(h, 1.0, &W1, 0.5);
@@ -606,24 +666,29 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
     commutator_A(h, X1, Op2{&V, 1.0, &W2, 0.5}, t1, t2, O1, O2, true, &pc);
   }
   // second-order amplitudes (Eqs. T1_2nd, T2_2nd) and [H(0), A(2)]
+  ws.tag = "second-order";
   Tensor U1, U2, V1, V2;
   amplitudes(h, &O1, O2, U1, U2, V1, V2);
   // [W, A(1)]_{1,2}
+  ws.tag = "Q";
   Tensor Q1, Q2;
   {
     Tensor Y1 = build_x1(h, 0.0, &W1, 1.0);
     Op1Pieces pc = op1_pieces(h, 0.0, &W1, 1.0);
     commutator_A(h, Y1, Op2{nullptr, 0.0, &W2, 1.0}, t1, t2, Q1, Q2, false, &pc);
   }
-  // Htilde(2)_{1,2} excitation blocks = [H0, A(2)] + O - [W, A(1)] / 6
-  Tensor Z1 = mk(h, {P, H}), Z2 = mk(h, {P, P, H, H});
-  axpy(ws, 1.0, V1.v, "ai", Z1, "ai");
+  // Htilde(2)_{1,2} excitation blocks = [H0, A(2)] + O - [W, A(1)] / 6,
+  // accumulated in place of [H0, A(2)] (not needed otherwise)
+  ws.tag = "Z";
+  Tensor Z1 = std::move(V1), Z2 = std::move(V2);
   axpy(ws, 1.0, O1.v, "ai", Z1, "ai");
   axpy(ws, -1.0 / 6.0, Q1.v, "ai", Z1, "ai");
-  axpy(ws, 1.0, V2.v, "abij", Z2, "abij");
   axpy(ws, 1.0, O2.v, "abij", Z2, "abij");
   axpy(ws, -1.0 / 6.0, Q2.v, "abij", Z2, "abij");
+  Q1.release();
+  Q2.release();
   Tensor Zx1 = build_x1(h, 0.0, &Z1, 1.0);
+  ws.tag = "E3";
   int r2 = ws.nresults;
   scalar(h, Xs1, Xs2, U1, U2);
   int r3 = ws.nresults;
@@ -636,6 +701,7 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   h.O1 = std::move(O1);
   h.O2 = std::move(O2);
   h.launches = ws.launches;
+  ws.tag = "";
 }
 
 }  // namespace dsrg

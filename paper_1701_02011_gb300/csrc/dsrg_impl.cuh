@@ -19,6 +19,9 @@ struct Handle {
   double* blk[9] = {};  // g1a g1b l2aa l2ab l2bb l3aaa l3aab l3abb l3bbb
   // reference quantities on spin orbitals
   Tensor gam, eta, L2, L3, F1;
+  // active blocks of gamma and eta minus the identity ([A, A]): dressing a
+  // copy of X adds (M - 1) X on the active rows
+  Tensor gam_dI, eta_dI;
   // intermediates of the last evaluation
   Tensor T1, T2, T1b, T2b, O1, O2;
   long long launches = 0;
@@ -41,6 +44,7 @@ Tensor vclass(Handle& h, const Iv* ivs, double coef);
 Tensor build_x1(Handle& h, double c_v, const Tensor* W1, double c_w);
 void build_v(Handle& h, unsigned classes, Sym2& V);
 Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M);
+Tensor dress(Handle& h, Tensor&& X, int slot, const Tensor& M);  // in place on a temporary
 void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tensor& T2, Tensor& W1, Tensor& W2);
 void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef);
 struct Op1Pieces;

@@ -51,7 +51,7 @@ void Workspace::prof_reset() {
 int Workspace::begin(int id, double flops, double bytes) {
   launches++;
   if (!profiling) return -1;
-  Rec r{id, nullptr, nullptr, flops, bytes, 0, 0, 0};
+  Rec r{id, nullptr, nullptr, flops, bytes, 0, 0, 0, tag};
   for (cudaEvent_t* e : {&r.a, &r.b}) {
     if (!ev_pool.empty()) {
       *e = ev_pool.back();
@@ -83,9 +83,9 @@ void Workspace::prof_collect() {
     std::sort(order.begin(), order.end(), [](auto& x, auto& y) { return x.first > y.first; });
     for (int i = 0; i < (int)order.size() && i < atoi(top); ++i) {
       const Rec& r = recs[order[i].second];
-      fprintf(stderr, "[dsrg] %-10s %9.3f ms  M=%lld N=%lld K=%lld  %.3f TFLOP/s %.0f GB/s\n", kernel_name(r.id),
+      fprintf(stderr, "[dsrg] %-10s %9.3f ms  M=%lld N=%lld K=%lld  %.3f TFLOP/s %.0f GB/s  %s\n", kernel_name(r.id),
               order[i].first, r.m, r.n, r.k, r.flops / (order[i].first * 1e-3) / 1e12,
-              r.bytes / (order[i].first * 1e-3) / 1e9);
+              r.bytes / (order[i].first * 1e-3) / 1e9, r.tag ? r.tag : "");
     }
   }
   for (auto& r : recs) {
@@ -521,6 +521,34 @@ void axpy(Workspace& ws, double alpha, const View& A, const char* la, Tensor& C,
     if (blk.n == kMaxBlocks) flush();
   }
   flush();
+}
+
+Tensor alias_permuted(Tensor& T, const int* perm) {
+  Tensor a;
+  a.v.p = T.v.p;
+  a.v.rank = T.v.rank;
+  a.v.mask = 0;
+  for (int k = 0; k < T.v.rank; ++k) {
+    a.v.iv[k] = T.v.iv[perm[k]];
+    a.v.st[k] = T.v.st[perm[k]];
+    a.v.ss[k] = T.v.ss[perm[k]];
+  }
+  for (int b = 0; b < (1 << T.v.rank); ++b) {
+    if (!((T.v.mask >> b) & 1)) continue;
+    int ab = 0;
+    for (int k = 0; k < T.v.rank; ++k) ab |= ((b >> perm[k]) & 1) << k;
+    a.v.mask |= 1ULL << ab;
+  }
+  return a;  // ws == nullptr: never returned to the workspace
+}
+
+void merge_alias_mask(Tensor& T, const Tensor& alias, const int* perm) {
+  for (int ab = 0; ab < (1 << T.v.rank); ++ab) {
+    if (!((alias.v.mask >> ab) & 1)) continue;
+    int b = 0;
+    for (int k = 0; k < T.v.rank; ++k) b |= ((ab >> k) & 1) << perm[k];
+    T.v.mask |= 1ULL << b;
+  }
 }
 
 void dot(Workspace& ws, double alpha, const View& A, const char* la, const View& B, const char* lb) {

@@ -80,7 +80,8 @@ class Workspace {
   int slices = 0;
   // opt-in per-launch timing
   bool profiling = false;
-  struct Rec { int id; cudaEvent_t a, b; double flops, bytes; long long m, n, k; };
+  const char* tag = "";  // step of the energy being issued (profile output only)
+  struct Rec { int id; cudaEvent_t a, b; double flops, bytes; long long m, n, k; const char* tag; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> ev_pool;
   long long prof_launches[K_NKERNELS] = {0};
@@ -97,7 +98,20 @@ class Workspace {
   size_t in_use_ = 0, peak_ = 0;
 };
 
+// Names the step issued while it is in scope (restores the outer name).
+struct ProfTag {
+  Workspace& ws;
+  const char* prev;
+  ProfTag(Workspace& w, const char* t) : ws(w), prev(w.tag) { w.tag = t; }
+  ~ProfTag() { ws.tag = prev; }
+};
+
 Tensor make_tensor(Workspace& ws, int rank, const Iv* ivs, bool zero = true);
+// Non-owning view of T with slots permuted (slot k of the alias is slot
+// perm[k] of T), its mask permuted alike; merge_alias_mask carries the
+// blocks written through the alias back into T's mask.
+Tensor alias_permuted(Tensor& T, const int* perm);
+void merge_alias_mask(Tensor& T, const Tensor& alias, const int* perm);
 // Mask of a tensor whose first rank/2 slots are creators and the rest
 // annihilators: non-zero only when the alpha counts agree.
 uint64_t conserving_mask(int rank);

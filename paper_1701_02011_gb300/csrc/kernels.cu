@@ -560,6 +560,10 @@ __global__ void __launch_bounds__(DOT_THREADS) k_dot_blocks(const NdArgs g, cons
   }
 }
 
+__global__ void k_add_diagonal(double* D, int n, double v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) D[(long long)i * n + i] += v;
+}
+
 __global__ void k_fill(double* p, long long n, double v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -862,6 +866,11 @@ void launch_dot_blocks(const NdArgs& g0, double alpha, const DotBlocks& p, doubl
   const dim3 grid((unsigned)gx, (unsigned)p.n);
   if (nd_prepare(g)) k_dot_blocks<true><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
   else k_dot_blocks<false><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
+}
+
+void launch_add_diagonal(double* D, int n, double v, cudaStream_t st) {
+  if (n <= 0) return;
+  k_add_diagonal<<<1, 256, 0, st>>>(D, n, v);
 }
 
 void launch_fill(double* p, long long n, double v, cudaStream_t st) {

@@ -125,6 +125,8 @@ void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, const FlatTable& tab
 // kind 0: generic contraction, 1: DF build of (pr|qs), 2: ladder contraction
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind = 0);
 void launch_fill(double* p, long long n, double v, cudaStream_t st);
+// D[i][i] += v for the n x n row-major D
+void launch_add_diagonal(double* D, int n, double v, cudaStream_t st);
 
 // Reference quantities on spin orbitals.
 //   gamma over H = core + active (2h x 2h): identity on core, g1 on active;
