@@ -70,6 +70,16 @@ def aggregate(per_rank_seconds, steps, world):
     return world * steps / t, t
 
 
+def max_over_ranks(dist, seconds, device="cuda"):
+    """The slowest rank's timed region (every rank must call it)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------
 # clocks during the timed region
 # ----------------------------------------------------------------------------
@@ -275,11 +285,7 @@ def run_ours(args, rank, world, local_rank):
                                                           args.precision, args.slices, ClockSampler(local_rank))
     if dist:
         dist.barrier()
-    total_s = sum(ms) / 1000.0
-    if dist:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(dist, sum(ms) / 1000.0)
     value, tmax = aggregate([total_s], args.steps, world)
     ms_per_step = 1000.0 * tmax / args.steps
     # ---- end to end: host buffers (pinned), copies inside the timed region

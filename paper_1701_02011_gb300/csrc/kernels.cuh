@@ -31,10 +31,19 @@ inline FastDiv make_fastdiv(unsigned d) {
   return f;
 }
 #ifdef __CUDACC__
-__device__ __forceinline__ unsigned fast_div(unsigned n, const FastDiv& f) {
-  return (unsigned)(((unsigned long long)__umulhi(n, f.mlo) + n) >> f.l);
-}
+__host__ __device__ __forceinline__
+#else
+inline
 #endif
+    unsigned
+    fast_div(unsigned n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  const unsigned hi = __umulhi(n, f.mlo);
+#else
+  const unsigned hi = (unsigned)(((unsigned long long)n * f.mlo) >> 32);
+#endif
+  return (unsigned)(((unsigned long long)hi + n) >> f.l);
+}
 
 // C[m, n] += alpha * sum_k A[m, k] B[k, n] over multi-indices m, n, k and a
 // batch multi-index b present in all three operands.  Every group holds up

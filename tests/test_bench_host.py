@@ -1,0 +1,57 @@
+"""Host logic of the multi-GPU bench (one instance per rank, weak scaling):
+two gloo ranks on the CPU run the same reduction the GPU ranks run over NCCL."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+import synth
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, lr = bench.rank_env()
+    seconds = 1.0 + 0.5 * r  # rank 1 is the slow one
+    t = bench.max_over_ranks(dist, seconds, device="cpu")
+    value, tmax = bench.aggregate([t], 5, w)
+    inst = synth.config_instance("cas44_c2_v12_q60",
+                                 seed=synth.CONFIGS["cas44_c2_v12_q60"]["seed"] + bench.instance_seed_offset(r))
+    out[r] = (r, w, lr, t, value, tmax, float(np.asarray(inst["B"]).sum()))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_weak_scaling():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+        res = [out[r] for r in range(world)]
+    for r, (rr, w, lr, t, value, tmax, bsum) in enumerate(res):
+        assert (rr, w, lr) == (r, world, r)
+        assert t == pytest.approx(1.5)  # max over ranks, seen by every rank
+        assert tmax == pytest.approx(1.5)
+        assert value == pytest.approx(world * 5 / 1.5)  # all ranks' energies / slowest time
+    # every rank evaluates its own instance of the same sizes
+    assert res[0][6] != res[1][6]
+
+
+def test_aggregate_single_rank():
+    v, t = bench.aggregate([2.0], 4, 1)
+    assert (v, t) == (2.0, 2.0)
+    assert bench.instance_seed_offset(0) == 0 and bench.instance_seed_offset(3) == 3000
