@@ -203,6 +203,8 @@ int dsrg_split_gemm(long long M, long long N, long long K, const double *A, long
  *   "T1b" [2p][2h], "T2b" [2p][2p][2h][2h]     second-order amplitudes
  *   "O1" [2p][2h], "O2" [2p][2p][2h][2h]       excitation blocks of
  *                                              1/2 [Htilde(1), A(1)]_{1,2}
+ * Spin blocks that change the number of alpha electrons are zero (the library
+ * does not store them and fills them in on the copy).
  * Returns DSRG_ERR_ARG for an unknown name or a wrong count.
  */
 int dsrg_fetch(const dsrg_handle *h, const char *name, double *dst, long long count);

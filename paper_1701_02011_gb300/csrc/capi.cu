@@ -87,8 +87,8 @@ void load_inputs(dsrg::Handle& h, const dsrg_inputs* in) {
   }
   {
     Iv a4[4] = {h.A, h.A, h.A, h.A}, a6[6] = {h.A, h.A, h.A, h.A, h.A, h.A};
-    h.L2 = make_tensor(h.ws, 4, a4, true);
-    h.L3 = make_tensor(h.ws, 6, a6, true);
+    h.L2 = make_tensor(h.ws, 4, a4, true, true);  // dense: built whole by k_cumulant
+    h.L3 = make_tensor(h.ws, 6, a6, true, true);
     if (na > 0) {
       const double* b2[4] = {h.blk[2], h.blk[3], h.blk[4], nullptr};
       const double* b3[4] = {h.blk[5], h.blk[6], h.blk[7], h.blk[8]};
@@ -122,7 +122,7 @@ void load_inputs(dsrg::Handle& h, const dsrg_inputs* in) {
           g.sb[1] = h.F1.v.st[1];
           g.total = (long long)g.e[0] * g.e[1];
           launch_axpy(g, 1.0, h.f1raw + (long long)lo[bi] * n + lo[bj],
-                      h.F1.v.p + s * (h.F1.v.ss[0] + h.F1.v.ss[1]) + lo[bi] * h.F1.v.st[0] + lo[bj] * h.F1.v.st[1],
+                      h.F1.v.p + h.F1.v.boff[s * 3] + lo[bi] * h.F1.v.st[0] + lo[bj] * h.F1.v.st[1],
                       st);
         }
     h.F1.v.mask = conserving_mask(2);
@@ -320,10 +320,25 @@ int dsrg_fetch(const dsrg_handle* hd, const char* name, double* dst, long long c
   else if (!strcmp(name, "O2")) t = &h.O2;
   else return fail(DSRG_ERR_ARG, std::string("unknown tensor ") + name);
   if (!t->v.p) return fail(DSRG_ERR_STATE, std::string(name) + " has not been computed");
-  if ((long long)t->n != count) return fail(DSRG_ERR_ARG, "element count mismatch");
-  cudaError_t e = cudaMemcpyAsync(dst, t->v.p, t->n * sizeof(double), cudaMemcpyDeviceToHost, h.stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h.stream);
-  if (e != cudaSuccess) return fail(DSRG_ERR_CUDA, cudaGetErrorString(e));
+  // the dense spin-major layout: every spin block, blocks not stored are zero
+  long long dense = 1;
+  for (int k = 0; k < t->v.rank; ++k) dense *= 2LL * t->v.iv[k].len();
+  if (dense != count) return fail(DSRG_ERR_ARG, "element count mismatch");
+  try {
+    dsrg::Handle& hm = *hd->h;
+    dsrg::Tensor d = dsrg::make_tensor(hm.ws, t->v.rank, t->v.iv, true, true);
+    const char* lab = "abcdef";
+    char l[8] = {0};
+    for (int k = 0; k < t->v.rank; ++k) l[k] = lab[k];
+    dsrg::View src = t->v;
+    src.mask = src.stored;  // copy every stored block
+    dsrg::axpy(hm.ws, 1.0, src, l, d, l);
+    dsrg::check_cuda(cudaMemcpyAsync(dst, d.v.p, d.n * sizeof(double), cudaMemcpyDeviceToHost, h.stream),
+                     "cudaMemcpyAsync (fetch)");
+    dsrg::check_cuda(cudaStreamSynchronize(h.stream), "cudaStreamSynchronize (fetch)");
+  } catch (const std::exception& ex) {
+    return fail(classify(ex), ex.what());
+  }
   return DSRG_OK;
 }
 

@@ -22,6 +22,13 @@ Tensor mk(Handle& h, std::initializer_list<Iv> ivs, bool zero = true) {
   return make_tensor(h.ws, (int)v.size(), v.data(), zero);
 }
 
+// every spin block stored: for intermediates whose spin conservation pairs
+// other slots than (first half | second half)
+Tensor mk_dense(Handle& h, std::initializer_list<Iv> ivs) {
+  std::vector<Iv> v(ivs);
+  return make_tensor(h.ws, (int)v.size(), v.data(), true, true);
+}
+
 void raw_axpy4(Handle& h, double alpha, const double* src, const long long* ss, double* dst, const long long* ds,
                const int* ext) {
   NdArgs g{};
@@ -82,9 +89,10 @@ Tensor vclass(Handle& h, const Iv* ivs, double coef) {
   const View& v = V.v;
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) {
-      double* dJ = v.p + a * v.ss[0] + b * v.ss[1] + a * v.ss[2] + b * v.ss[3];
+      // spin block bits: slot k has spin bit k
+      double* dJ = v.p + v.boff[a | b << 1 | a << 2 | b << 3];
       raw_axpy4(h, coef, J, sJ, dJ, v.st, L);
-      double* dK = v.p + a * v.ss[0] + b * v.ss[1] + b * v.ss[2] + a * v.ss[3];
+      double* dK = v.p + v.boff[a | b << 1 | b << 2 | a << 3];
       raw_axpy4(h, -coef, K, sK, dK, v.st, L);
     }
   V.v.mask = conserving_mask(4);
@@ -226,7 +234,18 @@ void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tenso
   W2 = mk(h, {h.P, h.P, h.H, h.H}, false);
   {
     int r = h.ws.begin(K_AMP, 0.0, 24.0 * (double)T2.n);
-    launch_amp2(h.nc, h.na, h.nv, h.s, h.eps, O2.v.p, T2.v.p, W2.v.p, h.ws.stream);
+    Amp2Layout lay{};
+    for (int b = 0; b < 16; ++b) {
+      lay.boff[b] = ((T2.v.stored >> b) & 1) ? T2.v.boff[b] : -1;
+      if (((T2.v.stored >> b) & 1) != ((O2.v.stored >> b) & 1) || ((T2.v.stored >> b) & 1 && T2.v.boff[b] != O2.v.boff[b]))
+        throw std::runtime_error("amplitudes: O2 and T2 layouts differ");
+    }
+    for (int k = 0; k < 4; ++k) {
+      lay.st[k] = T2.v.st[k];
+      if (O2.v.st[k] != T2.v.st[k] || O2.v.iv[k].lo != T2.v.iv[k].lo || O2.v.iv[k].hi != T2.v.iv[k].hi)
+        throw std::runtime_error("amplitudes: O2 and T2 layouts differ");
+    }
+    launch_amp2(h.nc, h.na, h.nv, h.s, h.eps, O2.v.p, T2.v.p, W2.v.p, lay, h.ws.stream);
     h.ws.end(r);
   }
   T2.v.mask = W2.v.mask = conserving_mask(4);
@@ -252,7 +271,7 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
   const int p = h.na + h.nv, hh = h.nc + h.na;
   if (p == 0 || hh == 0) return;
   const View& tv = T2.v;
-  const double* t = tv.p + tv.ss[1] + tv.ss[3];
+  const double* t = tv.p + tv.boff[0b1010];  // spins (alpha, beta, alpha, beta)
   size_t capL;
   size_t nL = (size_t)p * p * hh * hh;
   double* L = h.ws.get(nL, capL);
@@ -271,7 +290,11 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
   long long sL[4] = {(long long)p * hh * hh, (long long)hh * hh, hh, 1};
   long long sLji[4] = {sL[0], sL[1], 1, hh};      // L[p,q,j,i]
   long long sLqp[4] = {sL[1], sL[0], hh, 1};      // L[q,p,i,j]
-  auto blk = [&](int a, int b, int i, int j) { return c.p + a * c.ss[0] + b * c.ss[1] + i * c.ss[2] + j * c.ss[3]; };
+  auto blk = [&](int a, int b, int i, int j) {
+    const int bits = a | b << 1 | i << 2 | j << 3;
+    if (!((c.stored >> bits) & 1)) throw std::runtime_error("ladder: spin block not stored");
+    return c.p + c.boff[bits];
+  };
   raw_axpy4(h, coef, L, sL, blk(0, 1, 0, 1), c.st, ext);
   raw_axpy4(h, coef, L, sL, blk(1, 0, 1, 0), c.st, ext);
   raw_axpy4(h, -coef, L, sLji, blk(0, 1, 1, 0), c.st, ext);
@@ -304,17 +327,8 @@ static Op1Pieces op1_pieces(Handle& h, double c_f, const Tensor* W1, double c_w)
   if (W1 && c_w != 0.0) {
     o.v[o.n] = W1->v;
     o.c[o.n++] = c_w;
-    View t;
-    t.rank = 2;
-    t.p = W1->v.p;
-    t.iv[0] = W1->v.iv[1];
-    t.iv[1] = W1->v.iv[0];
-    t.st[0] = W1->v.st[1];
-    t.st[1] = W1->v.st[0];
-    t.ss[0] = W1->v.ss[1];
-    t.ss[1] = W1->v.ss[0];
-    t.mask = W1->v.mask;  // spin-diagonal: symmetric under the swap
-    o.v[o.n] = t;
+    const int swap[2] = {1, 0};
+    o.v[o.n] = W1->v.permuted(swap);
     o.c[o.n++] = c_w;
   }
   return o;
@@ -404,7 +418,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
       contract_x2(ws, -0.5, X2, "pqrs", Z.v, "qr", C1, "ps");
     }
     {
-      Tensor Y = mk(h, {P, H, A, A});
+      Tensor Y = mk_dense(h, {P, H, A, A});  // conserves a + s = i + q
       contract(ws, 1.0, T2.v, "abij", L2.v, "qbjs", Y, "aiqs");
       contract_x2(ws, -1.0, X2, "pqas", Y.v, "aiqs", C1, "pi");
     }
@@ -424,7 +438,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
       contract(ws, -0.25, Y.v, "piab", T2.v, "abij", C1, "pj");
     }
     {
-      Tensor Y = mk(h, {P, H, A, A});
+      Tensor Y = mk_dense(h, {P, H, A, A});  // conserves b + r = i + p
       contract(ws, 1.0, T2.v, "abij", L2.v, "pajr", Y, "bipr");
       contract_x2(ws, -1.0, X2, "pirs", Y.v, "bipr", C1, "bs");
     }

@@ -24,6 +24,24 @@ View View::sub(const Iv* want) const {
   return o;
 }
 
+View View::permuted(const int* perm) const {
+  View o = *this;
+  o.stored = 0;
+  o.mask = 0;
+  for (int k = 0; k < rank; ++k) {
+    o.iv[k] = iv[perm[k]];
+    o.st[k] = st[perm[k]];
+  }
+  for (int ob = 0; ob < (1 << rank); ++ob) {
+    int b = 0;
+    for (int k = 0; k < rank; ++k) b |= ((ob >> k) & 1) << perm[k];
+    o.boff[ob] = boff[b];
+    if ((stored >> b) & 1) o.stored |= 1ULL << ob;
+    if ((mask >> b) & 1) o.mask |= 1ULL << ob;
+  }
+  return o;
+}
+
 const char* kernel_name(int id) {
   switch (id) {
     case K_GEMM: return "k_gemm<0>";
@@ -283,18 +301,47 @@ void Tensor::release() {
   cap = 0;
 }
 
-Tensor make_tensor(Workspace& ws, int rank, const Iv* ivs, bool zero) {
+Tensor make_tensor(Workspace& ws, int rank, const Iv* ivs, bool zero, bool dense) {
   Tensor t;
   t.v.rank = rank;
-  long long stride = 1;
+  const bool sparse = !dense && rank >= 4 && rank % 2 == 0;
+  long long block = 1;  // elements of one spin block
   for (int k = rank - 1; k >= 0; --k) {
     t.v.iv[k] = ivs[k];
-    int L = ivs[k].len() > 0 ? ivs[k].len() : 0;
-    t.v.st[k] = stride;
-    t.v.ss[k] = (long long)L * stride;
-    stride *= 2LL * L;
+    const int L = ivs[k].len() > 0 ? ivs[k].len() : 0;
+    block *= L;
   }
-  t.n = (size_t)stride;
+  for (int b = 0; b < (1 << kMaxRank); ++b) t.v.boff[b] = kNoBlock;
+  long long stride = 1;
+  if (sparse) {
+    // spatial strides inside a block; the stored blocks one after another
+    for (int k = rank - 1; k >= 0; --k) {
+      t.v.st[k] = stride;
+      stride *= ivs[k].len() > 0 ? ivs[k].len() : 0;
+    }
+    t.v.stored = conserving_mask(rank);
+    long long nb = 0;
+    for (int b = 0; b < (1 << rank); ++b)
+      if ((t.v.stored >> b) & 1) t.v.boff[b] = nb++ * block;
+    t.n = (size_t)(nb * block);
+  } else {
+    // spin-major slots: index (sigma, x) -> sigma * len + x
+    long long ss[kMaxRank];
+    for (int k = rank - 1; k >= 0; --k) {
+      const int L = ivs[k].len() > 0 ? ivs[k].len() : 0;
+      t.v.st[k] = stride;
+      ss[k] = (long long)L * stride;
+      stride *= 2LL * L;
+    }
+    t.v.stored = rank >= 6 ? ~0ULL : ((1ULL << (1 << rank)) - 1);
+    for (int b = 0; b < (1 << rank); ++b) {
+      long long o = 0;
+      for (int k = 0; k < rank; ++k)
+        if ((b >> k) & 1) o += ss[k];
+      t.v.boff[b] = o;
+    }
+    t.n = (size_t)stride;
+  }
   t.ws = &ws;
   t.v.p = ws.get(t.n, t.cap);
   if (zero) check_cuda(cudaMemsetAsync(t.v.p, 0, t.n * sizeof(double), ws.stream), "memset");
@@ -360,11 +407,10 @@ inline int spin_bits(const View& X, const char* lx, const std::vector<Lab>& L, i
   return b;
 }
 
-inline long long spin_off(const View& X, int bits) {
-  long long o = 0;
-  for (int k = 0; k < X.rank; ++k)
-    if ((bits >> k) & 1) o += X.ss[k];
-  return o;
+inline long long spin_off(const View& X, int bits, const char* labels = "") {
+  if (!((X.stored >> bits) & 1))
+    throw std::runtime_error(std::string("spin block ") + std::to_string(bits) + " of '" + labels + "' not stored");
+  return X.boff[bits];
 }
 
 struct Dim {
@@ -443,7 +489,7 @@ bool contract(Workspace& ws, double alpha, const View& A, const char* la, const 
   for (int assign = 0; assign < (1 << L.size()); ++assign) {
     int ba = spin_bits(a, la, L, assign), bb = spin_bits(b, lb, L, assign), bc = spin_bits(c, lc, L, assign);
     if (!((a.mask >> ba) & 1) || !((b.mask >> bb) & 1)) continue;
-    pairs.push_back({spin_off(a, ba), spin_off(b, bb), spin_off(c, bc)});
+    pairs.push_back({spin_off(a, ba, la), spin_off(b, bb, lb), spin_off(c, bc, lc)});
     C.v.mask |= 1ULL << bc;
   }
   if (pairs.empty()) return false;
@@ -515,7 +561,7 @@ void axpy(Workspace& ws, double alpha, const View& A, const char* la, Tensor& C,
     int ba = spin_bits(a, la, L, assign), bc = spin_bits(c, lc, L, assign);
     if (!((a.mask >> ba) & 1)) continue;
     blk.a[blk.n] = a.p + spin_off(a, ba);
-    blk.c[blk.n] = c.p + spin_off(c, bc);
+    blk.c[blk.n] = c.p + spin_off(c, bc, lc);
     ++blk.n;
     C.v.mask |= 1ULL << bc;
     if (blk.n == kMaxBlocks) flush();
@@ -525,20 +571,7 @@ void axpy(Workspace& ws, double alpha, const View& A, const char* la, Tensor& C,
 
 Tensor alias_permuted(Tensor& T, const int* perm) {
   Tensor a;
-  a.v.p = T.v.p;
-  a.v.rank = T.v.rank;
-  a.v.mask = 0;
-  for (int k = 0; k < T.v.rank; ++k) {
-    a.v.iv[k] = T.v.iv[perm[k]];
-    a.v.st[k] = T.v.st[perm[k]];
-    a.v.ss[k] = T.v.ss[perm[k]];
-  }
-  for (int b = 0; b < (1 << T.v.rank); ++b) {
-    if (!((T.v.mask >> b) & 1)) continue;
-    int ab = 0;
-    for (int k = 0; k < T.v.rank; ++k) ab |= ((b >> perm[k]) & 1) << k;
-    a.v.mask |= 1ULL << ab;
-  }
+  a.v = T.v.permuted(perm);
   return a;  // ws == nullptr: never returned to the workspace
 }
 
@@ -608,23 +641,9 @@ bool Sym2::resolve(const Iv* want, View& out, double& sign) const {
       for (int k = 0; k < 4 && ok; ++k) ok = t.v.iv[k].contains(want[pm[k]]);
       if (!ok) continue;
       // request slot j is class slot k with pm[k] == j
-      View v;
-      v.rank = 4;
-      v.p = t.v.p;
-      for (int k = 0; k < 4; ++k) {
-        int j = pm[k];
-        v.p += (long long)(want[j].lo - t.v.iv[k].lo) * t.v.st[k];
-        v.iv[j] = want[j];
-        v.st[j] = t.v.st[k];
-        v.ss[j] = t.v.ss[k];
-      }
-      v.mask = 0;
-      for (int b = 0; b < 16; ++b) {
-        if (!((t.v.mask >> b) & 1)) continue;
-        int vb = 0;
-        for (int k = 0; k < 4; ++k) vb |= ((b >> k) & 1) << pm[k];
-        v.mask |= 1ULL << vb;
-      }
+      int inv[4];
+      for (int k = 0; k < 4; ++k) inv[pm[k]] = k;
+      View v = t.v.permuted(inv).sub(want);
       out = v;
       sign = kSign[o];
       return true;
@@ -645,22 +664,7 @@ static void x2_request(const char* lx, const std::vector<Lab>& L, Iv* want) {
 View w_place(const Tensor& W, int herm) {
   static const int hp[4] = {2, 3, 0, 1};
   if (!herm) return W.v;
-  View v;
-  v.rank = 4;
-  v.p = W.v.p;
-  for (int j = 0; j < 4; ++j) {
-    v.iv[j] = W.v.iv[hp[j]];
-    v.st[j] = W.v.st[hp[j]];
-    v.ss[j] = W.v.ss[hp[j]];
-  }
-  v.mask = 0;
-  for (int b = 0; b < 16; ++b) {
-    if (!((W.v.mask >> b) & 1)) continue;
-    int vb = 0;
-    for (int j = 0; j < 4; ++j) vb |= ((b >> hp[j]) & 1) << j;
-    v.mask |= 1ULL << vb;
-  }
-  return v;
+  return W.v.permuted(hp);
 }
 
 static bool v_view(const Op2& X, const Iv* want, View& xv, double& sg, const char* what, bool skip) {

@@ -26,14 +26,24 @@ inline Iv isect(Iv a, Iv b) { return Iv{a.lo > b.lo ? a.lo : b.lo, a.hi < b.hi ?
 
 constexpr int kMaxRank = 6;
 
+// Spin blocks: block b has spin (bit k of b) on slot k.  A tensor stores
+// either every block (dense: rank <= 2 and the cumulants) or only the blocks
+// that conserve the alpha count between its first and second half of slots
+// (creators | annihilators): 6 of 16 for rank 4.  Each stored block is a
+// dense row-major array over the slots' spatial intervals.
+constexpr long long kNoBlock = -1;
+
 struct View {
-  double* p = nullptr;  // element with every slot at (spin 0, iv.lo)
+  double* p = nullptr;  // spatial origin: every slot at iv.lo, block offset 0
   int rank = 0;
   Iv iv[kMaxRank];
-  long long st[kMaxRank] = {0};  // stride of the spatial index
-  long long ss[kMaxRank] = {0};  // stride of the spin index
-  uint64_t mask = 0;              // bit b set: spin block with spins (bit k of b) may be non-zero
+  long long st[kMaxRank] = {0};      // stride of the spatial index within a block
+  long long boff[1 << kMaxRank] = {};  // offset of stored block b from p (kNoBlock if absent)
+  uint64_t stored = 0;               // blocks present in memory
+  uint64_t mask = 0;                 // blocks that may be non-zero (a subset of stored)
   View sub(const Iv* want) const;
+  // the same data with slot k of the result being slot perm[k] of this view
+  View permuted(const int* perm) const;
 };
 
 class Workspace;
@@ -106,7 +116,9 @@ struct ProfTag {
   ~ProfTag() { ws.tag = prev; }
 };
 
-Tensor make_tensor(Workspace& ws, int rank, const Iv* ivs, bool zero = true);
+// dense: store every spin block (else rank >= 4 tensors keep only the
+// alpha-conserving blocks)
+Tensor make_tensor(Workspace& ws, int rank, const Iv* ivs, bool zero = true, bool dense = false);
 // Non-owning view of T with slots permuted (slot k of the alias is slot
 // perm[k] of T), its mask permuted alike; merge_alias_mask carries the
 // blocks written through the alias back into T's mask.

@@ -579,15 +579,15 @@ __device__ __forceinline__ double regulariser(double s, double D) {
   return -expm1(-x) / D;
 }
 
-// One thread per spatial (a, b, i, j): D and R(D) once, then the 16 spin
-// blocks (sa, sb, si, sj) of the [2p][2p][2h][2h] arrays; blocks that change
-// the number of alpha electrons are written as zeros.  Consecutive threads
-// take consecutive j (contiguous within a spin block).
+// One thread per spatial (a, b, i, j): D and R(D) once, then every stored
+// spin block (sa, sb, si, sj) of the [P,P,H,H] arrays (block bits sa | sb<<1 |
+// si<<2 | sj<<3, offsets lay.boff, spatial strides lay.st; the three arrays
+// share the layout).  Consecutive threads take consecutive j.
 __global__ void k_amp2(int nc, int na, int nv, double s, const double* __restrict__ eps,
-                       const double* __restrict__ O2, double* __restrict__ T2, double* __restrict__ W2) {
+                       const double* __restrict__ O2, double* __restrict__ T2, double* __restrict__ W2,
+                       const Amp2Layout lay) {
   const int h = nc + na, p = na + nv;
   const unsigned hh = (unsigned)h * h, total = (unsigned)p * p * hh;
-  const long long P2 = 2LL * p, H2 = 2LL * h;
   for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     const unsigned ab = idx / hh, ij = idx - ab * hh;
     const int a = (int)(ab / p), b = (int)(ab - (unsigned)a * p);
@@ -595,10 +595,13 @@ __global__ void k_amp2(int nc, int na, int nv, double s, const double* __restric
     const bool internal = (i >= nc) && (j >= nc) && (a < na) && (b < na);
     const double D = eps[i] + eps[j] - eps[nc + a] - eps[nc + b];
     const double R = internal ? 0.0 : regulariser(s, D);
+    const long long sp0 = a * lay.st[0] + b * lay.st[1] + i * lay.st[2] + j * lay.st[3];
 #pragma unroll
-    for (int sp = 0; sp < 16; ++sp) {
-      const int sa = sp >> 3 & 1, sb = sp >> 2 & 1, si = sp >> 1 & 1, sj = sp & 1;
-      const long long o = (((sa * p + a) * P2 + (sb * p + b)) * H2 + (si * h + i)) * H2 + (sj * h + j);
+    for (int bits = 0; bits < 16; ++bits) {
+      const long long bo = lay.boff[bits];
+      if (bo < 0) continue;
+      const long long o = bo + sp0;
+      const int sa = bits & 1, sb = bits >> 1 & 1, si = bits >> 2 & 1, sj = bits >> 3 & 1;
       double t = 0.0;
       if (sa + sb == si + sj) t = O2[o] * R;
       T2[o] = t;
@@ -894,11 +897,11 @@ void launch_build_cumulant(int na, int rank, const double* const* blk_dev, doubl
 }
 
 void launch_amp2(int nc, int na, int nv, double s, const double* eps, const double* O2, double* T2, double* W2,
-                 cudaStream_t st) {
+                 const Amp2Layout& lay, cudaStream_t st) {
   long long h = nc + na, p = na + nv;
   long long n = p * p * h * h;  // spatial quadruples, one thread each
   if (n >= (1LL << 32)) throw std::runtime_error("amplitudes: p^2 h^2 must stay below 2^32");
-  k_amp2<<<grid_for(n, 256), 256, 0, st>>>(nc, na, nv, s, eps, O2, T2, W2);
+  k_amp2<<<grid_for(n, 256), 256, 0, st>>>(nc, na, nv, s, eps, O2, T2, W2, lay);
 }
 
 void launch_amp1(int nc, int na, int nv, double s, const double* eps, const double* O1, const double* S,

@@ -148,10 +148,16 @@ void launch_build_cumulant(int na, int rank, const double* const* blk_dev, doubl
                            cudaStream_t st);
 
 // Amplitudes of Eqs. T2_1st / T2_2nd and the closed form of [H0, A]:
-//   T2 = O2 * R(D) (zero if all four indices are active), W2 = -D * T2.
-// Layout [2p][2p][2h][2h] with P = [c, n) and H = [0, c + a) in global orbitals.
+//   T2 = O2 * R(D) (zero if all four indices are active), W2 = -D * T2, on
+// every stored spin block of the [P,P,H,H] layout (P = [c, n), H = [0, c + a)).
+// spin-block offsets (block bits: slot k spin at bit k; < 0 = not stored) and
+// spatial strides of a [P,P,H,H] array
+struct Amp2Layout {
+  long long boff[16];
+  long long st[4];
+};
 void launch_amp2(int nc, int na, int nv, double s, const double* eps, const double* O2,
-                 double* T2, double* W2, cudaStream_t st);
+                 double* T2, double* W2, const Amp2Layout& lay, cudaStream_t st);
 // T1 = (O1 + S) * R(D), W1 = -D * T1 + S; layout [2p][2h].
 void launch_amp1(int nc, int na, int nv, double s, const double* eps, const double* O1,
                  const double* S, double* T1, double* W1, cudaStream_t st);
