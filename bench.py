@@ -383,6 +383,113 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_scan(args, rank, world, local_rank):
+    """The 32-point scan of uneven instances (core 4-12, CAS(4,4) or CAS(6,6),
+    virtual 60-200, auxiliary 4 x virtual, virtual gap shrinking along the
+    scan) through the batched call: every instance's energy captured once as
+    a CUDA graph, a batch's graphs replayed at once on their own streams.
+    Points are grouped into batches whose handles fit the device memory
+    budget (a handle keeps its captured energy's buffers).  Ranks take
+    disjoint scan points (weak scaling over points)."""
+    import numpy as np
+    import torch
+
+    import paper_1701_02011_gb300 as g
+    import synth
+    from paper_1701_02011_gb300 import build as libbuild
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    libbuild.build()
+    points = [j for j in range(32) if j % world == rank]
+    insts = [synth.scan_instance(j) for j in points]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def est_bytes(inst):
+        # device footprint of one energy: the stored [P,P,P,H] class of V plus
+        # about twenty [P,P,H,H] tensors, six spin blocks each
+        p, h = inst["na"] + inst["nv"], inst["nc"] + inst["na"]
+        return 48.0 * p ** 3 * h + 20 * 48.0 * p * p * h * h + 3e8
+
+    groups, cur, used = [], [], 0.0
+    for k in sorted(range(len(insts)), key=lambda k: -est_bytes(insts[k])):
+        b = est_bytes(insts[k])
+        if cur and used + b > args.scan_budget_gb * 1e9:
+            groups.append(cur)
+            cur, used = [], 0.0
+        cur.append(k)
+        used += b
+    if cur:
+        groups.append(cur)
+
+    def timed(prec, slices, steps):
+        """Per batch: handles, one call that warms up and captures, then the
+        timed replays; the batch's handles are freed before the next batch."""
+        energies = [None] * len(insts)
+        tot = [0.0] * steps
+        launches = peak = 0
+        for grp in groups:
+            devs = [{k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
+                     for k, v in insts[i].items()} for i in grp]
+            streams = [torch.cuda.Stream() for _ in devs]
+            hs = [g.Dsrg(d, stream=st.cuda_stream, precision=prec, slices=slices) for d, st in zip(devs, streams)]
+            e = g.dsrg_pt3_batch(hs)  # eager warm-up, capture, first replay
+            for _ in range(max(args.warmup - 1, 0)):
+                e = g.dsrg_pt3_batch(hs)
+            for s in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                if dist:
+                    dist.barrier()
+                t0 = time.perf_counter()
+                e = g.dsrg_pt3_batch(hs)  # host-synchronous: every energy is back on the host
+                tot[s] += time.perf_counter() - t0
+            for i, ei in zip(grp, e):
+                energies[i] = ei
+            launches += sum(g.dsrg_last_launch_count(h.h) for h in hs)
+            peak = max(peak, sum(g.dsrg_peak_bytes(h.h) for h in hs))
+            for h in hs:
+                h.close()
+            del devs
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        return energies, tot, launches, peak
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    e_split, ts, launches, peak = timed(g.DSRG_PREC_SPLIT, args.slices, args.steps)
+    clk = clocks.stop()
+    total_s = max_over_ranks(dist, sum(ts))
+    value, tmax = aggregate([total_s], args.steps * len(points), world)
+    cmp = None
+    if not args.no_comparison:
+        e64, ts64, _, peak64 = timed(g.DSRG_PREC_FP64, 0, 1)
+        errs = {k: max(abs(a[k] - b[k]) for a, b in zip(e_split, e64)) for k in ("e2", "e3a", "e3b", "e3")}
+        cmp = {"precision": "fp64", "s_per_scan": statistics.median(ts64),
+               "value": len(points) / statistics.median(ts64), "max_abs_headline_minus_comparison_Eh": errs,
+               "peak_bytes": peak64}
+    line = {
+        "metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split bf16 tensor-core products)",
+        "data": "synthetic (seeded; see DESIGN.md)",
+        "config": {"workload": "scan32", "instances": 32, "per_rank": len(points), "precision": "split",
+                   "slices": args.slices, "batches": [len(gp) for gp in groups],
+                   "graph": "one CUDA graph per instance, a batch's graphs replayed concurrently",
+                   "l2": "flushed (256 MiB write) before each timed batch"},
+        "note": "a step evaluates every scan point of the rank: one batched call per memory batch, host-synchronous",
+        "clocks": clk, "gpu_launches": launches * args.steps, "peak_bytes": peak, "comparison": cmp,
+        "energies_e3": [e["e3"] for e in e_split],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,10 +503,16 @@ def main(argv=None):
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--no-comparison", action="store_true",
                     help="skip timing the other precision (quick runs, profiler launch lists)")
+    ap.add_argument("--workload", choices=(WORKLOAD, "scan32"), default=WORKLOAD,
+                    help="the CAS(6,6) instance (default) or the batched 32-point scan")
+    ap.add_argument("--scan-budget-gb", type=float, default=120.0,
+                    help="device memory per scan batch (handles keep their captured buffers)")
     args = ap.parse_args(argv)
     rank, world, local_rank = rank_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "scan32":
+        run_scan(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

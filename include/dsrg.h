@@ -109,6 +109,25 @@ int dsrg_pt2(dsrg_handle *h, dsrg_energies *out);
 /* E(2) and E(3) components.  Synchronises the handle's stream. */
 int dsrg_pt3(dsrg_handle *h, dsrg_energies *out);
 
+/*
+ * PT3 energies of n independent instances (the points of a potential-energy
+ * scan, any sizes), all in flight at once: handle i's energy runs on its own
+ * stream and out[i] receives it.  No counterpart in the paper, which
+ * evaluates points one by one; this is the batching of the hot path.  The
+ * first call for a handle evaluates one energy eagerly (filling the handle's
+ * buffer cache) and captures the energy as a CUDA graph; later calls replay
+ * the graphs only, so the host issues n launches instead of thousands.  A
+ * handle's graph is dropped by dsrg_pt2/dsrg_pt3 on it (eager evaluation) and
+ * by dsrg_load (new inputs); the next batch call captures it again.  Every
+ * handle keeps the device buffers of its captured energy, so the batch needs
+ * the sum of the handles' peak memory (dsrg_peak_bytes).  The handles must be
+ * distinct; handles sharing a stream run one after another.
+ * Ownership: the caller keeps hs and out.  Errors: DSRG_ERR_ARG (n < 0, NULL
+ * arrays, a repeated handle), DSRG_ERR_STATE (NULL handle), otherwise as
+ * dsrg_pt3; after an error some out[i] may be unset.
+ */
+int dsrg_pt3_batch(dsrg_handle *const *hs, int n, dsrg_energies *out);
+
 /* Release all device memory of the handle (NULL is ignored). */
 void dsrg_free(dsrg_handle *h);
 

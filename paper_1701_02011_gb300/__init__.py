@@ -43,7 +43,7 @@ class dsrg_energies(ctypes.Structure):
                 ("e3", ctypes.c_double)]
 
 
-EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_free", "dsrg_last_error",
+EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_pt3_batch", "dsrg_free", "dsrg_last_error",
            "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
            "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc", "dsrg_split_gemm")
 
@@ -65,6 +65,8 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
     for f in ("dsrg_pt2", "dsrg_pt3"):
         getattr(L, f).argtypes = [ctypes.c_void_p, ctypes.POINTER(dsrg_energies)]
         getattr(L, f).restype = ctypes.c_int
+    L.dsrg_pt3_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(dsrg_energies)]
+    L.dsrg_pt3_batch.restype = ctypes.c_int
     L.dsrg_free.argtypes = [ctypes.c_void_p]
     L.dsrg_free.restype = None
     L.dsrg_last_error.argtypes = []
@@ -170,6 +172,17 @@ def dsrg_pt2(h) -> dict:
 
 def dsrg_pt3(h) -> dict:
     return _energies(load_library().dsrg_pt3, h)
+
+
+def dsrg_pt3_batch(handles) -> list:
+    """PT3 energies of several handles at once (graph-captured after the first
+    call per handle); handles are raw handles or Dsrg objects."""
+    hs = [x.h if isinstance(x, Dsrg) else x for x in handles]
+    n = len(hs)
+    arr = (ctypes.c_void_p * max(n, 1))(*hs)
+    out = (dsrg_energies * max(n, 1))()
+    _check(load_library().dsrg_pt3_batch(arr, n, out))
+    return [{"e2": e.e2, "e3a": e.e3a, "e3b": e.e3b, "e3": e.e3} for e in list(out)[:n]]
 
 
 def dsrg_free(h) -> None:

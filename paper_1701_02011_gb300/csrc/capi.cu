@@ -187,10 +187,12 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
     h->ws.cap_results = 1 << 16;
     dsrg::check_cuda(cudaMalloc(&h->ws.results, h->ws.cap_results * sizeof(double)), "cudaMalloc (results)");
     h->ws.dot_scratch_len = 2 * 152 * 16;
-    dsrg::check_cuda(cudaMalloc(&h->ws.dot_scratch, (h->ws.dot_scratch_len + 2) * sizeof(double)),
+    // dot partials, then the dot's ticket and the split kernels' status flag
+    dsrg::check_cuda(cudaMalloc(&h->ws.dot_scratch, (h->ws.dot_scratch_len + 4) * sizeof(double)),
                      "cudaMalloc (scratch)");
     h->ws.dot_ticket = reinterpret_cast<unsigned*>(h->ws.dot_scratch + h->ws.dot_scratch_len);
-    dsrg::check_cuda(cudaMemsetAsync(h->ws.dot_ticket, 0, 2 * sizeof(double), st), "cudaMemsetAsync (ticket)");
+    h->ws.oz_status = reinterpret_cast<int*>(h->ws.dot_scratch + h->ws.dot_scratch_len + 2);
+    dsrg::check_cuda(cudaMemsetAsync(h->ws.dot_ticket, 0, 4 * sizeof(double), st), "cudaMemsetAsync (ticket)");
     load_inputs(*h, in);
     dsrg::check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize (init)");
   } catch (const std::exception& e) {
@@ -219,6 +221,8 @@ int dsrg_load(dsrg_handle* hd, const dsrg_inputs* in) {
   if (in->nc != h.nc || in->na != h.na || in->nv != h.nv || in->naux != h.naux)
     return fail(DSRG_ERR_ARG, "dsrg_load needs the sizes the handle was created with");
   try {
+    h.drop_graph();  // the captured energy refers to the old reference tensors
+    h.warm = false;
     h.s = in->s;
     load_inputs(h, in);
   } catch (const std::exception& e) {
@@ -227,28 +231,108 @@ int dsrg_load(dsrg_handle* hd, const dsrg_inputs* in) {
   return DSRG_OK;
 }
 
+namespace {
+void reset_status(dsrg::Handle& h) {
+  if (h.ws.slices > 0)
+    dsrg::check_cuda(cudaMemsetAsync(h.ws.oz_status, 0, sizeof(int), h.stream), "status reset");
+}
+
+void check_status(dsrg::Handle& h) {
+  dsrg::check_cuda(cudaGetLastError(), "kernel launch");
+  if (h.ws.slices > 0 && dsrg::ozaki_status(h.stream, h.ws.oz_status))
+    throw std::runtime_error("CUDA: a bounded wait in the split-precision kernel ran out");
+}
+
+void eager_energy(dsrg::Handle& h, bool pt3, dsrg_energies* out) {
+  h.drop_graph();  // the handle's tensors move to new buffers
+  double e2 = 0, e3a = 0, e3b = 0;
+  reset_status(h);
+  dsrg::run_energy(h, pt3, &e2, &e3a, &e3b);
+  check_status(h);
+  h.warm = true;
+  h.ws.prof_collect();
+  out->e2 = e2;
+  out->e3a = e3a;
+  out->e3b = e3b;
+  out->e3 = e3a + e3b;
+}
+
+// Capture one PT3 energy of h (status reset included) as a CUDA graph.  The
+// workspace cache is warm, so the captured buffers are the ones the eager
+// energy used; they stay reserved by the handle until the graph is dropped.
+void capture_energy(dsrg::Handle& h) {
+  const bool prof = h.ws.profiling;
+  h.ws.profiling = false;
+  dsrg::check_cuda(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture");
+  cudaGraph_t g = nullptr;
+  try {
+    reset_status(h);
+    dsrg::issue_energy(h, true);
+  } catch (...) {
+    cudaStreamEndCapture(h.stream, &g);
+    if (g) cudaGraphDestroy(g);
+    h.ws.profiling = prof;
+    throw;
+  }
+  h.ws.profiling = prof;
+  dsrg::check_cuda(cudaStreamEndCapture(h.stream, &g), "cudaStreamEndCapture");
+  cudaError_t e = cudaGraphInstantiate(&h.graph, g, 0ULL);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h.graph = nullptr;
+    dsrg::check_cuda(e, "cudaGraphInstantiate");
+  }
+  h.graph_gen = h.ws.generation;
+}
+}  // namespace
+
 static int run(dsrg_handle* hd, bool pt3, dsrg_energies* out) {
   g_last_error.clear();
   if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
   if (!out) return fail(DSRG_ERR_ARG, "out is NULL");
   try {
-    double e2 = 0, e3a = 0, e3b = 0;
-    if (hd->h->ws.slices > 0) {
-      int zero = 0;
-      dsrg::check_cuda(cudaMemcpyToSymbolAsync(dsrg::g_oz_status_alias(), &zero, sizeof(int), 0,
-                                               cudaMemcpyHostToDevice, hd->h->stream),
-                       "status reset");
+    eager_energy(*hd->h, pt3, out);
+  } catch (const std::exception& e) {
+    return fail(classify(e), e.what());
+  }
+  return DSRG_OK;
+}
+
+int dsrg_pt3_batch(dsrg_handle* const* hs, int n, dsrg_energies* out) {
+  g_last_error.clear();
+  if (n < 0) return fail(DSRG_ERR_ARG, "n < 0");
+  if (n == 0) return DSRG_OK;
+  if (!hs || !out) return fail(DSRG_ERR_ARG, "handles and out are required");
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i] || !hs[i]->h) return fail(DSRG_ERR_STATE, "NULL handle in the batch");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(DSRG_ERR_ARG, "a handle appears twice in the batch");
+  }
+  try {
+    // graphs: captured once per handle (after one eager energy), replayed after
+    for (int i = 0; i < n; ++i) {
+      dsrg::Handle& h = *hs[i]->h;
+      if (h.graph && h.graph_gen != h.ws.generation) h.drop_graph();
+      if (!h.graph) {
+        if (!h.warm) eager_energy(h, true, &out[i]);
+        capture_energy(h);
+      }
     }
-    dsrg::run_energy(*hd->h, pt3, &e2, &e3a, &e3b);
-    dsrg::check_cuda(cudaGetLastError(), "kernel launch");
-    if (hd->h->ws.slices > 0 && dsrg::ozaki_status(hd->h->stream))
-      return fail(DSRG_ERR_CUDA, "a bounded wait in the split-precision kernel ran out");
-    dsrg::check_cuda(cudaStreamSynchronize(hd->h->stream), "cudaStreamSynchronize");
-    hd->h->ws.prof_collect();
-    out->e2 = e2;
-    out->e3a = e3a;
-    out->e3b = e3b;
-    out->e3 = e3a + e3b;
+    // every handle's energy in flight at once, each on its own stream
+    for (int i = 0; i < n; ++i) {
+      dsrg::Handle& h = *hs[i]->h;
+      dsrg::check_cuda(cudaGraphLaunch(h.graph, h.stream), "cudaGraphLaunch");
+    }
+    for (int i = 0; i < n; ++i) {
+      dsrg::Handle& h = *hs[i]->h;
+      double e2 = 0, e3a = 0, e3b = 0;
+      dsrg::finish_energy(h, &e2, &e3a, &e3b);
+      check_status(h);
+      out[i].e2 = e2;
+      out[i].e3a = e3a;
+      out[i].e3b = e3b;
+      out[i].e3 = e3a + e3b;
+    }
   } catch (const std::exception& e) {
     return fail(classify(e), e.what());
   }

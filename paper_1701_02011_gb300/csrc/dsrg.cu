@@ -614,28 +614,14 @@ void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const 
   }
 }
 
-// sum of the device result slots [lo, hi) (compensated, on the host)
-static double sum_results(Handle& h, int lo, int hi) {
-  if (hi <= lo) return 0.0;
-  std::vector<double> v(hi - lo);
-  h.d2h_bytes += (long long)(hi - lo) * (long long)sizeof(double);
-  check_cuda(cudaMemcpyAsync(v.data(), h.ws.results + lo, (hi - lo) * sizeof(double), cudaMemcpyDeviceToHost,
-                             h.ws.stream),
-             "copy results");
-  check_cuda(cudaStreamSynchronize(h.ws.stream), "sync");
-  long double s = 0.0L;
-  for (double x : v) s += x;
-  return (double)s;
-}
-
-// ---------------------------------------------------------------------------
-// the energy (Sec. II.B)
-// ---------------------------------------------------------------------------
-void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
+// Every kernel and copy of one energy, enqueued on the handle's stream with
+// no host synchronisation (so that it can be captured in a CUDA graph); the
+// result-slot ranges of E(2), E3a, E3b go to h.res.
+void issue_energy(Handle& h, bool pt3) {
   Workspace& ws = h.ws;
   ws.launches = 0;
   ws.nresults = 0;
-  h.d2h_bytes = 0;
+  h.res_pt3 = pt3;
   const Iv& H = h.H;
   const Iv& P = h.P;
   // first-order amplitudes from the non-diagonal part of H(1)
@@ -657,14 +643,12 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   ws.tag = "E2";
   Tensor Xs1 = build_x1(h, 2.0, &W1, 1.0);
   Op2 Xs2{&V, 2.0, &W2, 1.0};
-  int r0 = ws.nresults;
+  h.res[0] = ws.nresults;
   scalar(h, Xs1, Xs2, T1, T2);
-  int r1 = ws.nresults;
-  *e2 = sum_results(h, r0, r1);
+  h.res[1] = h.res[2] = h.res[3] = h.res[4] = ws.nresults;
   h.T1 = std::move(T1);
   h.T2 = std::move(T2);
   if (!pt3) {
-    *e3a = *e3b = 0.0;
     h.launches = ws.launches;
     ws.tag = "";
     return;
@@ -703,19 +687,43 @@ void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
   Q2.release();
   Tensor Zx1 = build_x1(h, 0.0, &Z1, 1.0);
   ws.tag = "E3";
-  int r2 = ws.nresults;
+  h.res[2] = ws.nresults;
   scalar(h, Xs1, Xs2, U1, U2);
-  int r3 = ws.nresults;
+  h.res[3] = ws.nresults;
   scalar(h, Zx1, Op2{nullptr, 0.0, &Z2, 1.0}, t1, t2);
-  int r4 = ws.nresults;
-  *e3a = sum_results(h, r2, r3);
-  *e3b = sum_results(h, r3, r4);
+  h.res[4] = ws.nresults;
   h.T1b = std::move(U1);
   h.T2b = std::move(U2);
   h.O1 = std::move(O1);
   h.O2 = std::move(O2);
   h.launches = ws.launches;
   ws.tag = "";
+}
+
+static double sum_slots(const std::vector<double>& v, int lo, int hi) {
+  long double t = 0.0L;
+  for (int i = lo; i < hi; ++i) t += v[i];
+  return (double)t;
+}
+
+// One copy of the result slots of the last issued energy, summed on the host
+// (long double) per component.  Synchronises the stream.
+void finish_energy(Handle& h, double* e2, double* e3a, double* e3b) {
+  const int n = h.res[4];
+  std::vector<double> v((size_t)(n > 0 ? n : 0));
+  h.d2h_bytes = (long long)n * (long long)sizeof(double);
+  if (n > 0)
+    check_cuda(cudaMemcpyAsync(v.data(), h.ws.results, n * sizeof(double), cudaMemcpyDeviceToHost, h.ws.stream),
+               "copy results");
+  check_cuda(cudaStreamSynchronize(h.ws.stream), "sync");
+  *e2 = sum_slots(v, h.res[0], h.res[1]);
+  *e3a = h.res_pt3 ? sum_slots(v, h.res[2], h.res[3]) : 0.0;
+  *e3b = h.res_pt3 ? sum_slots(v, h.res[3], h.res[4]) : 0.0;
+}
+
+void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {
+  issue_energy(h, pt3);
+  finish_energy(h, e2, e3a, e3b);
 }
 
 }  // namespace dsrg

@@ -26,6 +26,19 @@ struct Handle {
   Tensor T1, T2, T1b, T2b, O1, O2;
   long long launches = 0;
   long long d2h_bytes = 0;
+  // result-slot boundaries of the last issued energy: E(2) [res0, res1),
+  // E3a [res2, res3), E3b [res3, res4)
+  int res[5] = {0, 0, 0, 0, 0};
+  bool res_pt3 = false;
+  // the PT3 energy captured as a CUDA graph (batch calls); stale when the
+  // workspace generation changes or the handle runs eagerly / reloads
+  cudaGraphExec_t graph = nullptr;
+  unsigned long long graph_gen = 0;
+  bool warm = false;  // one eager energy has filled the workspace cache
+  void drop_graph() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+  }
   // raw device buffers taken from the workspace (returned on destruction)
   std::vector<std::pair<double*, size_t>> owned;
   double* own(size_t n) {
@@ -36,6 +49,7 @@ struct Handle {
   }
   explicit Handle(cudaStream_t st) : stream(st), ws(st) {}
   ~Handle() {
+    drop_graph();
     for (auto& b : owned) ws.put(b.first, b.second);
   }
 };
@@ -54,5 +68,7 @@ void commutator_A(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, 
                   Tensor& O2, bool df, const Op1Pieces* X1p);
 void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2);
 void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b);
+void issue_energy(Handle& h, bool pt3);
+void finish_energy(Handle& h, double* e2, double* e3a, double* e3b);
 
 }  // namespace dsrg

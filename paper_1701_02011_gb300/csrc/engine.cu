@@ -261,6 +261,7 @@ double* Workspace::get(size_t n, size_t& cap) {
       cudaGetLastError();
       for (auto& b : free_) cudaFree(b.p);
       free_.clear();
+      ++generation;
       check_cuda(cudaMalloc(&p, n * sizeof(double)), "cudaMalloc");
     }
   }

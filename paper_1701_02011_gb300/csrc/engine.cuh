@@ -84,6 +84,8 @@ class Workspace {
   double* dot_scratch = nullptr;  // dot_scratch_len doubles, then the ticket of the one-launch dot
   int dot_scratch_len = 0;
   unsigned* dot_ticket = nullptr;  // zero between launches
+  int* oz_status = nullptr;        // split-precision kernels' error flag (device; nullptr: file-scope flag)
+  unsigned long long generation = 0;  // bumped when cached blocks are freed (captured graphs go stale)
   long long launches = 0;
   // > 0: large contractions run as split-precision tensor-core products with
   // this many 7-bit digit slices per operand; 0: FP64 everywhere

@@ -7,6 +7,7 @@
 #include "ozaki.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace dsrg {
 namespace {
@@ -689,13 +690,27 @@ size_t oz_smem_bytes(int S, int BN) {
   return (tiles > stage ? tiles : stage) + 1024;
 }
 
+// the largest dynamic shared memory any launch of k_ozaki_mma<BN> asks for,
+// set once per device (kept out of the launch path, which may be captured)
+template <int BN>
+void oz_smem_attribute() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  check_cuda(cudaFuncSetAttribute(k_ozaki_mma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 4096),
+             "cudaFuncSetAttribute (ozaki)");
+  done[dev] = true;
+}
+
 template <int BN>
 void oz_launch_bn(const OzArgs& a, int MT, int NT, cudaStream_t st) {
   // at least 120 KiB so that one CTA (one TMEM allocation) occupies an SM
   size_t smem = oz_smem_bytes(a.S, BN);
   if (smem < 120 * 1024) smem = 120 * 1024;
-  check_cuda(cudaFuncSetAttribute(k_ozaki_mma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-             "cudaFuncSetAttribute (ozaki)");
+  oz_smem_attribute<BN>();
   k_ozaki_mma<BN><<<dim3(MT, NT, a.splits > 1 ? a.splits : 1), OZ_THREADS, smem, st>>>(a);
   if (a.splits > 1) k_ozaki_reduce<BN><<<oz_grid(a.M * a.N), 256, 0, st>>>(a);
 }
@@ -709,9 +724,12 @@ void oz_launch_mma(const OzArgs& a, int MT, int NT, int BN, cudaStream_t st) {
 
 const void* g_oz_status_alias() { return (const void*)&g_oz_status; }
 
-int ozaki_status(cudaStream_t st) {
+int ozaki_status(cudaStream_t st, const int* flag) {
   int v = 0;
-  check_cuda(cudaMemcpyFromSymbolAsync(&v, g_oz_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st), "status");
+  if (flag)
+    check_cuda(cudaMemcpyAsync(&v, flag, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+  else
+    check_cuda(cudaMemcpyFromSymbolAsync(&v, g_oz_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st), "status");
   check_cuda(cudaStreamSynchronize(st), "sync");
   return v;
 }
@@ -868,7 +886,7 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
   a.N = N;
   a.alpha = g0.alpha;
   a.C = g0.C;
-  a.status = nullptr;
+  a.status = ws.oz_status;
   a.splits = splits;
   a.ktper = ktper;
   a.part = part;
@@ -938,7 +956,7 @@ extern "C" int dsrg_split_gemm(long long M, long long N, long long K, const doub
     g.nbatch = 1;
     ozaki_gemm(ws, g, slices, K_OZAKI_MMA);
     check_cuda(cudaGetLastError(), "split gemm launch");
-    if (ozaki_status(st)) return set_error(DSRG_ERR_CUDA, "split gemm: a bounded wait in the kernel ran out");
+    if (ozaki_status(st, nullptr)) return set_error(DSRG_ERR_CUDA, "split gemm: a bounded wait in the kernel ran out");
   } catch (const std::exception& e) {
     return set_error(DSRG_ERR_CUDA, e.what());
   }

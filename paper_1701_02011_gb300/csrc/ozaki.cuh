@@ -19,9 +19,9 @@ namespace dsrg {
 
 constexpr int kOzakiMaxSlices = 7;
 
-// Error status of the last split-precision contraction kernel (device flag
-// set when a bounded wait runs out); 0 = ok.
-int ozaki_status(cudaStream_t st);
+// Error status of the split-precision kernels (device flag set when a bounded
+// wait runs out; flag nullptr: the file-scope flag); 0 = ok.  Synchronises st.
+int ozaki_status(cudaStream_t st, const int* flag);
 // the status flag's symbol (for cudaMemcpyToSymbol)
 const void* g_oz_status_alias();
 

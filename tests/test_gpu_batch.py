@@ -1,0 +1,126 @@
+"""Batched energies (dsrg_pt3_batch): several instances of uneven sizes, each
+handle's energy captured once as a CUDA graph and then replayed, all
+handles in flight at once on their own streams."""
+import pytest
+
+import synth
+from oracle import dsrg
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("e2", "e3a", "e3b", "e3")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_02011_gb300 import build
+    build.build()
+    import paper_1701_02011_gb300 as g
+    g.load_library()
+    return g
+
+
+# uneven core / active / virtual / auxiliary sizes, like the points of a scan
+SMALL = [(1, 3, 2, 2, 5), (2, 2, 2, 3, 6), (2, 4, 4, 12, 60), (3, 4, 4, 21, 50), (2, 0, 0, 3, 6)]
+
+
+def _inst(shape, seed):
+    nc, na, nel, nv, naux = shape
+    return synth.make_instance(nc, na, nel, nv, naux, 0.5, seed=seed)
+
+
+def _streams(torch, n):
+    return [torch.cuda.Stream() for _ in range(n)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_batch_equals_eager_and_replays(lib, precision):
+    import torch
+    prec = lib.DSRG_PREC_FP64 if precision == "fp64" else lib.DSRG_PREC_SPLIT
+    sl = 0 if precision == "fp64" else 6
+    insts = [_inst(s, 100 + k) for k, s in enumerate(SMALL)]
+    st = _streams(torch, len(insts))
+    eager = []
+    for inst, s in zip(insts, st):
+        h = lib.Dsrg(inst, stream=s.cuda_stream, precision=prec, slices=sl)
+        eager.append(h.pt3())
+        h.close()
+    hs = [lib.Dsrg(inst, stream=s.cuda_stream, precision=prec, slices=sl) for inst, s in zip(insts, st)]
+    try:
+        first = lib.dsrg_pt3_batch(hs)   # eager warm-up + capture + replay
+        second = lib.dsrg_pt3_batch(hs)  # replay only
+        for a, b, c in zip(eager, first, second):
+            for k in KEYS:
+                assert b[k] == a[k], (k, a[k], b[k])  # same kernels in the same order
+                assert c[k] == a[k], (k, a[k], c[k])
+        # new inputs on one handle: its graph is dropped and captured again
+        new = _inst(SMALL[2], 999)
+        hs[2].load(new)
+        third = lib.dsrg_pt3_batch(hs)
+        ref = lib.Dsrg(new, precision=prec, slices=sl)
+        e_new = ref.pt3()
+        ref.close()
+        for k in KEYS:
+            assert third[2][k] == e_new[k]
+            assert third[0][k] == eager[0][k]
+        # an eager call in between drops that handle's graph; the batch still agrees
+        e_mid = hs[0].pt3()
+        fourth = lib.dsrg_pt3_batch(hs)
+        for k in KEYS:
+            assert fourth[0][k] == e_mid[k] == eager[0][k]
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_batch_matches_oracle(lib):
+    import torch
+    insts = [_inst(s, 200 + k) for k, s in enumerate(SMALL[:4])]
+    st = _streams(torch, len(insts))
+    hs = [lib.Dsrg(inst, stream=s.cuda_stream) for inst, s in zip(insts, st)]
+    try:
+        lib.dsrg_pt3_batch(hs)
+        got = lib.dsrg_pt3_batch(hs)
+    finally:
+        for h in hs:
+            h.close()
+    for inst, e in zip(insts, got):
+        ref = dsrg.dsrg_pt3(inst)
+        for k in KEYS:
+            assert abs(e[k] - ref[k]) < 1e-9, (k, e[k], ref[k])
+
+
+def test_batch_argument_errors(lib):
+    inst = _inst(SMALL[0], 5)
+    h = lib.Dsrg(inst)
+    try:
+        with pytest.raises(lib.DsrgError):
+            lib.dsrg_pt3_batch([h, h])  # a handle twice
+        assert lib.dsrg_pt3_batch([]) == []
+    finally:
+        h.close()
+
+
+def test_scan_points_split_vs_fp64(lib):
+    """Points of the 32-point scan (uneven sizes, shrinking virtual gap) in one
+    batch: the split path with 7 slices within 1e-6 Eh of FP64 per component
+    (the scan's energies reach 4e4 Eh, where 6 slices leave ~4e-6)."""
+    import torch
+    points = [18, 23, 31, 13, 24]
+    insts = [synth.scan_instance(j) for j in points]
+    res = {}
+    for prec, sl in ((lib.DSRG_PREC_FP64, 0), (lib.DSRG_PREC_SPLIT, 7)):
+        st = _streams(torch, len(insts))
+        hs = [lib.Dsrg(inst, stream=s.cuda_stream, precision=prec, slices=sl) for inst, s in zip(insts, st)]
+        try:
+            lib.dsrg_pt3_batch(hs)
+            res[prec] = lib.dsrg_pt3_batch(hs)
+        finally:
+            for h in hs:
+                h.close()
+    for a, b in zip(res[lib.DSRG_PREC_SPLIT], res[lib.DSRG_PREC_FP64]):
+        for k in KEYS:
+            assert abs(a[k] - b[k]) < 1e-6, (k, a[k], b[k])
