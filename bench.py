@@ -213,13 +213,14 @@ def alg_flops(inst):
     return {"ladder": h * (h + 1) * p ** 4, "build": Q * p * p * (p * p + 1)}
 
 
-def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, clocks=None):
+def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, clocks=None, tune=False):
     """Warm up, then time `steps` PT3 energies (CUDA events on the library's
     stream around each step, L2 flushed before each step), then run one more
     energy with per-kernel events for the kernel breakdown (kept out of the
     timed steps, whose launches it would slow down)."""
     prec = g.DSRG_PREC_SPLIT if precision == "split" else g.DSRG_PREC_FP64
-    h = g.Dsrg(dev, stream=stream.cuda_stream, precision=prec, slices=slices if precision == "split" else 0)
+    h = g.Dsrg(dev, stream=stream.cuda_stream, precision=prec, slices=slices if precision == "split" else 0,
+               tune=tune and precision == "split")  # tuning happens in the first warm-up energy
     energies = None
     for _ in range(max(warmup, 0)):
         energies = h.pt3()
@@ -277,12 +278,13 @@ def run_ours(args, rank, world, local_rank):
     ms2 = e_other = None
     if not args.no_comparison:
         h2, ms2, e_other, stats2, _, _ = _time_path(g, torch, dev, stream, flush, max(1, min(args.steps, 3)),
-                                                    args.warmup, other, args.slices)
+                                                    args.warmup, other, args.slices, tune=not args.no_tune)
         h2.close()
     if dist:
         dist.barrier()
     h, ms, energies, stats, launches, clocks = _time_path(g, torch, dev, stream, flush, args.steps, args.warmup,
-                                                          args.precision, args.slices, ClockSampler(local_rank))
+                                                          args.precision, args.slices, ClockSampler(local_rank),
+                                                          tune=not args.no_tune)
     if dist:
         dist.barrier()
     total_s = max_over_ranks(dist, sum(ms) / 1000.0)
@@ -356,7 +358,8 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (split bf16 tensor-core products)",
         "data": "synthetic (seeded; see DESIGN.md)",
-        "config": dict(config_dict(inst, args.precision), slices=args.slices if args.precision == "split" else None),
+        "config": dict(config_dict(inst, args.precision), slices=args.slices if args.precision == "split" else None,
+                       tuned=(not args.no_tune) and args.precision == "split"),
         "effective_tflops_ladder_build": eff_tflops,
         "energies": energies,
         "comparison": None if ms2 is None else
@@ -435,7 +438,8 @@ def run_scan(args, rank, world, local_rank):
             devs = [{k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
                      for k, v in insts[i].items()} for i in grp]
             streams = [torch.cuda.Stream() for _ in devs]
-            hs = [g.Dsrg(d, stream=st.cuda_stream, precision=prec, slices=slices) for d, st in zip(devs, streams)]
+            hs = [g.Dsrg(d, stream=st.cuda_stream, precision=prec, slices=slices,
+                         tune=(not args.no_tune) and prec == g.DSRG_PREC_SPLIT) for d, st in zip(devs, streams)]
             e = g.dsrg_pt3_batch(hs)  # eager warm-up, capture, first replay
             for _ in range(max(args.warmup - 1, 0)):
                 e = g.dsrg_pt3_batch(hs)
@@ -477,7 +481,7 @@ def run_scan(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split bf16 tensor-core products)",
         "data": "synthetic (seeded; see DESIGN.md)",
         "config": {"workload": "scan32", "instances": 32, "per_rank": len(points), "precision": "split",
-                   "slices": args.slices, "batches": [len(gp) for gp in groups],
+                   "slices": args.slices, "batches": [len(gp) for gp in groups], "tuned": not args.no_tune,
                    "graph": "one CUDA graph per instance, a batch's graphs replayed concurrently",
                    "l2": "flushed (256 MiB write) before each timed batch"},
         "note": "a step evaluates every scan point of the rank: one batched call per memory batch, host-synchronous",
@@ -503,6 +507,8 @@ def main(argv=None):
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--no-comparison", action="store_true",
                     help="skip timing the other precision (quick runs, profiler launch lists)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="fixed tile/split rules for the split products (default: tuned in the first warm-up)")
     ap.add_argument("--workload", choices=(WORKLOAD, "scan32"), default=WORKLOAD,
                     help="the CAS(6,6) instance (default) or the batched 32-point scan")
     ap.add_argument("--scan-budget-gb", type=float, default=120.0,

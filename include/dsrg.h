@@ -86,6 +86,12 @@ typedef struct {
   void *stream;   /* cudaStream_t to run on; NULL = the library's own stream */
   int slices;     /* DSRG_PREC_SPLIT: 7-bit digit slices per operand (1..7);
                      0 selects 6                                             */
+  int tune;       /* DSRG_PREC_SPLIT: 1 = the first product of each new
+                     (M, N, K, slices) shape in the process times a few tile
+                     widths and k splits (on the caller's operands with
+                     alpha = 0, so nothing changes) and keeps the fastest;
+                     0 = fixed rules.  Results differ from the fixed rules
+                     only in summation order.  No counterpart in the paper. */
 } dsrg_options;
 
 typedef struct {

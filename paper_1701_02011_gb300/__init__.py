@@ -35,7 +35,8 @@ class dsrg_inputs(ctypes.Structure):
 
 
 class dsrg_options(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("slices", ctypes.c_int)]
+    _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("slices", ctypes.c_int),
+                ("tune", ctypes.c_int)]
 
 
 class dsrg_energies(ctypes.Structure):
@@ -146,10 +147,11 @@ def make_inputs(inst: dict):
     return s, keep
 
 
-def dsrg_init(inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0) -> ctypes.c_void_p:
+def dsrg_init(inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0,
+              tune: bool = False) -> ctypes.c_void_p:
     L = load_library()
     s, keep = make_inputs(inst)
-    opt = dsrg_options(precision, ctypes.c_void_p(stream) if stream else None, int(slices))
+    opt = dsrg_options(precision, ctypes.c_void_p(stream) if stream else None, int(slices), int(bool(tune)))
     h = ctypes.c_void_p()
     _check(L.dsrg_init(ctypes.byref(s), ctypes.byref(opt), ctypes.byref(h)))
     return h
@@ -280,9 +282,9 @@ def dsrg_split_gemm(A, B, C, alpha: float = 1.0, slices: int = 6, stream=None) -
 class Dsrg:
     """Convenience owner of one handle."""
 
-    def __init__(self, inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0):
+    def __init__(self, inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0, tune: bool = False):
         self.sizes = (int(inst["nc"]), int(inst["na"]), int(inst["nv"]))
-        self.h = dsrg_init(inst, stream, precision, slices)
+        self.h = dsrg_init(inst, stream, precision, slices, tune)
 
     def load(self, inst):
         dsrg_load(self.h, inst)

@@ -166,6 +166,7 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
   }
   h->own_stream = own;
   h->ws.slices = slices;
+  h->ws.tune = opts && opts->tune != 0;
   try {
     h->nc = in->nc;
     h->na = in->na;

@@ -85,6 +85,7 @@ class Workspace {
   int dot_scratch_len = 0;
   unsigned* dot_ticket = nullptr;  // zero between launches
   int* oz_status = nullptr;        // split-precision kernels' error flag (device; nullptr: file-scope flag)
+  bool tune = false;               // time tile/split candidates of new split-product shapes
   unsigned long long generation = 0;  // bumped when cached blocks are freed (captured graphs go stale)
   long long launches = 0;
   // > 0: large contractions run as split-precision tensor-core products with

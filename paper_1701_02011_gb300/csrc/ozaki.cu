@@ -7,7 +7,9 @@
 #include "ozaki.cuh"
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <vector>
 
 namespace dsrg {
 namespace {
@@ -741,7 +743,14 @@ bool ozaki_supported(const GemmArgs& g) {
   return g.M < (1LL << 31) && g.N < (1LL << 31) && g.K < (1LL << 31) && rows * groups < (1LL << 32);
 }
 
-void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
+namespace {
+// tile width (0: the rule below) and k-split mode (0: rule, 1: none, 2: twice the rule)
+struct OzChoice {
+  int bn = 0;
+  int split_mode = 0;
+};
+
+void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoice& ch) {
   if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0) return;
   if (g0.nbatch != 1) throw std::runtime_error("split-precision contraction needs nbatch == 1");
   if (S < 1 || S > kOzakiMaxSlices) throw std::runtime_error("split-precision slices must be 1..7");
@@ -799,7 +808,7 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
       a.cN[d] = g0.cM[d];
     }
   }
-  int BN = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  int BN = ch.bn ? ch.bn : N <= 32 ? 32 : N <= 64 ? 64 : 128;
   // shared memory per CTA is capped at 227 KiB (static arrays take up to 4 KiB)
   while (BN > 32 && oz_smem_bytes(S, BN) + 4096 > 227 * 1024) BN /= 2;
   const int MT = (int)((M + OZ_BM - 1) / OZ_BM), NT = (int)((N + BN - 1) / BN);
@@ -815,8 +824,9 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
   // spread a short output over more CTAs by splitting the k tiles
   int splits = 1, ktper = KT;
   const long long ctas = (long long)MT * NT;
-  if (ctas < 2 * 152 && KT >= 8) {
+  if (ch.split_mode != 1 && ctas < 2 * 152 && KT >= 8) {
     long long sp = (2 * 152 + ctas - 1) / ctas;
+    if (ch.split_mode == 2) sp *= 2;
     if (sp > KT / 4) sp = KT / 4;
     if (sp >= 2) {
       ktper = (KT + (int)sp - 1) / (int)sp;
@@ -906,6 +916,96 @@ void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
   ws.put(bufB, capB);
   ws.put(bufE, capE);
   if (part) ws.put(part, capP);
+}
+
+}  // namespace
+
+// Tile width and k split of a split product: fixed rules, or with ws.tune the
+// fastest of a few candidates, timed once per (M, N, K, slices) and device on
+// the caller's operands with alpha = 0 (C keeps its values bit for bit) and
+// cached for the process.  No timing while the stream is being captured.
+namespace {
+struct OzKey {
+  long long M, N, K;
+  int S, dev;
+  bool operator<(const OzKey& o) const {
+    if (M != o.M) return M < o.M;
+    if (N != o.N) return N < o.N;
+    if (K != o.K) return K < o.K;
+    if (S != o.S) return S < o.S;
+    return dev < o.dev;
+  }
+};
+std::mutex g_tune_mu;
+std::map<OzKey, OzChoice> g_tune;
+
+OzChoice choose(Workspace& ws, const GemmArgs& g0, int S, int kind) {
+  OzChoice def;
+  if (!ws.tune) return def;
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  const OzKey key{g0.M, g0.N, g0.K, S, dev};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  check_cuda(cudaStreamIsCapturing(ws.stream, &cs), "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) return def;
+  // candidates: tile widths up to about twice the shorter output side, and
+  // the k-split rule, no split, twice the rule when the rule splits
+  const long long nshort = g0.M < g0.N ? g0.M : g0.N;
+  const long long KT = (g0.K + OZ_BK - 1) / OZ_BK;
+  std::vector<OzChoice> cands;
+  for (int bn : {32, 64, 128}) {
+    if (bn != 32 && bn / 2 >= nshort) continue;
+    const long long big = g0.M > g0.N ? g0.M : g0.N;
+    const long long ctas = ((big + OZ_BM - 1) / OZ_BM) * ((nshort + bn - 1) / bn);
+    const bool splits = ctas < 2 * 152 && KT >= 8;
+    for (int sm = 0; sm < (splits ? 3 : 1); ++sm) {
+      OzChoice c;
+      c.bn = bn;
+      c.split_mode = sm;
+      cands.push_back(c);
+    }
+  }
+  GemmArgs gz = g0;
+  gz.alpha = 0.0;
+  const bool prof = ws.profiling;
+  const long long launches = ws.launches;
+  ws.profiling = false;
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+  check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+  OzChoice best = def;
+  float best_ms = 1e30f;
+  for (const OzChoice& c : cands) {
+    ozaki_run(ws, gz, S, kind, c);  // first run: packing buffers, caches
+    check_cuda(cudaEventRecord(e0, ws.stream), "cudaEventRecord");
+    ozaki_run(ws, gz, S, kind, c);
+    check_cuda(cudaEventRecord(e1, ws.stream), "cudaEventRecord");
+    check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ws.profiling = prof;
+  ws.launches = launches;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+}  // namespace
+
+void ozaki_gemm(Workspace& ws, const GemmArgs& g0, int S, int kind) {
+  if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0) return;
+  ozaki_run(ws, g0, S, kind, choose(ws, g0, S, kind));
 }
 
 }  // namespace dsrg

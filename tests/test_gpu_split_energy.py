@@ -51,3 +51,25 @@ def test_split_matches_fp64_at_the_bench_workload(lib):
         assert abs(es[k] - e64[k]) < 1e-6, (k, es[k], e64[k])
     # energies are O(1e3) Eh here: 1e-6 Eh is ~4e-10 relative
     assert abs(e64["e3"]) > 100.0
+
+
+def test_tuned_split_matches_fp64_and_is_reproducible(lib):
+    """With tile/split tuning on, the bench workload's split energy stays within
+    1 uEh of FP64; a second tuned handle takes the cached choices and gives
+    the same energies bit for bit."""
+    inst = synth.config_instance("cas66_c10_v100_q400")
+    a = lib.Dsrg(inst)
+    try:
+        e64 = a.pt3()
+    finally:
+        a.close()
+    res = []
+    for _ in range(2):
+        b = lib.Dsrg(inst, precision=lib.DSRG_PREC_SPLIT, slices=6, tune=True)
+        try:
+            res.append(b.pt3())
+        finally:
+            b.close()
+    for k in ("e2", "e3a", "e3b", "e3"):
+        assert abs(res[0][k] - e64[k]) < 1e-6, (k, res[0][k], e64[k])
+        assert res[1][k] == res[0][k]
