@@ -84,7 +84,7 @@ typedef struct {
 typedef struct {
   int precision;  /* DSRG_PREC_FP64 or DSRG_PREC_SPLIT                       */
   void *stream;   /* cudaStream_t to run on; NULL = the library's own stream */
-  int slices;     /* DSRG_PREC_SPLIT: 7-bit digit slices per operand (1..7);
+  int slices;     /* DSRG_PREC_SPLIT: 7-bit digit slices per operand (1..8);
                      0 selects 6                                             */
   int tune;       /* DSRG_PREC_SPLIT: 1 = the first product of each new
                      (M, N, K, slices) shape in the process times a few tile
@@ -206,7 +206,7 @@ int dsrg_df_ladder_noalloc(int n, int naux, int p0, int np, int nh, const double
  *   C[m][n] += alpha * sum_k A[m][k] B[k][n]
  * A [M][K] (row stride lda), B [K][N] (row stride ldb), C [M][N] (row stride
  * ldc), all FP64 device memory, row-major.  Every row of A and column of B is
- * scaled by a power of two and cut into `slices` (1..7) signed 7-bit digits
+ * scaled by a power of two and cut into `slices` (1..8) signed 7-bit digits
  * held exactly in BF16; digit products are accumulated exactly in FP32 over
  * 64-long chunks of k by tcgen05.mma and added into a two-float running sum,
  * so the result carries about 7*slices bits relative to the product of the

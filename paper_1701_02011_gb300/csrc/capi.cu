@@ -150,7 +150,7 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
   int slices = 0;
   if (opts && opts->precision == DSRG_PREC_SPLIT) {
     slices = opts->slices ? opts->slices : 6;
-    if (slices < 1 || slices > 7) return fail(DSRG_ERR_ARG, "slices must be 1..7");
+    if (slices < 1 || slices > 8) return fail(DSRG_ERR_ARG, "slices must be 1..8");
   }
   cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
   bool own = false;

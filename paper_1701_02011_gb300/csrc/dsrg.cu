@@ -12,6 +12,8 @@
 #include <vector>
 
 #include "dsrg_impl.cuh"
+
+#include <cstdlib>
 #include "ladder.cuh"
 
 namespace dsrg {
@@ -115,13 +117,32 @@ Tensor build_x1(Handle& h, double c_v, const Tensor* W1, double c_w) {
 }
 
 // V on the canonical classes HHHH, HHHP, HHPP, PHPH, PPPH (bits 0..4)
+// Classes larger than the budget (DSRG_V_CLASS_BUDGET_MB, default 8192 MB of
+// device memory per class) are not stored: the terms that read them build V
+// from B on their own intervals, a slab at a time within the same budget.
+// The [P,P,P,H] class is the one that grows past it (p^3 h: 53 GB at
+// p = 308, h = 38).
 void build_v(Handle& h, unsigned classes, Sym2& V) {
   V.cls.clear();
+  V.make = nullptr;
   const Iv& H = h.H;
   const Iv& P = h.P;
+  double budget_mb = 8192.0;
+  if (const char* env = getenv("DSRG_V_CLASS_BUDGET_MB")) budget_mb = atof(env);
+  const double budget = budget_mb * 1048576.0;
   Iv cl[5][4] = {{H, H, H, H}, {H, H, H, P}, {H, H, P, P}, {P, H, P, H}, {P, P, P, H}};
-  for (int c = 0; c < 5; ++c)
-    if ((classes >> c) & 1) V.cls.push_back(vclass(h, cl[c], 1.0));
+  for (int c = 0; c < 5; ++c) {
+    if (!((classes >> c) & 1)) continue;
+    double bytes = 6.0 * 8.0;  // six alpha-conserving spin blocks of doubles
+    for (int k = 0; k < 4; ++k) bytes *= cl[c][k].len() > 0 ? cl[c][k].len() : 0;
+    if (bytes <= budget) {
+      V.cls.push_back(vclass(h, cl[c], 1.0));
+    } else {
+      Handle* hp = &h;
+      V.make = [hp](const Iv* ivs) { return vclass(*hp, ivs, 1.0); };
+      V.max_elems = (long long)(budget / 8.0);
+    }
+  }
 }
 
 // out[..z..] = sum_x M[z,x] X[..x..] along one slot, M = gamma (hole range)

@@ -673,11 +673,34 @@ static bool v_view(const Op2& X, const Iv* want, View& xv, double& sg, const cha
   for (int k = 0; k < 4; ++k)
     if (want[k].lo < -100000000) throw std::runtime_error(std::string("unconstrained two-body label in ") + what);
   if (X.V->resolve(want, xv, sg)) return true;
-  if (skip) return false;
+  if (skip || X.V->make) return false;  // v_slabs serves classes that are not stored
   char buf[256];
   snprintf(buf, sizeof buf, "no stored two-body class covers [%d,%d)x[%d,%d)x[%d,%d)x[%d,%d) for %s", want[0].lo,
            want[0].hi, want[1].lo, want[1].hi, want[2].lo, want[2].hi, want[3].lo, want[3].hi, what);
   throw std::runtime_error(buf);
+}
+
+// V on the intervals `want` built on demand, one slab of the first slot at a
+// time; each slab's view goes to use().  The engine intersects label
+// intervals across operands, so every slab restricts the other operand and
+// the output to its own rows.  False when V keeps all its classes.
+template <class F>
+static bool v_slabs(const Op2& X, const Iv* want, F&& use) {
+  if (!X.V || !X.V->make || X.cv == 0.0) return false;
+  for (int k = 0; k < 4; ++k)
+    if (want[k].empty()) return true;
+  // per row of the first slot: the (pr|qs) and (ps|qr) blocks and six spin blocks
+  long long row = 8;
+  for (int k = 1; k < 4; ++k) row *= want[k].len();
+  long long rows = X.V->max_elems / row;
+  if (rows < 1) rows = 1;
+  for (int lo = want[0].lo; lo < want[0].hi; lo += (int)rows) {
+    const int hi = (long long)lo + rows < want[0].hi ? lo + (int)rows : want[0].hi;
+    Iv sub[4] = {Iv{lo, hi}, want[1], want[2], want[3]};
+    Tensor slab = X.V->make(sub);
+    use(slab.v);
+  }
+  return true;
 }
 
 bool contract_x2(Workspace& ws, double alpha, const Op2& X, const char* lx, const View& B, const char* lb, Tensor& C,
@@ -692,7 +715,12 @@ bool contract_x2(Workspace& ws, double alpha, const Op2& X, const char* lx, cons
   x2_request(lx, L, want);
   View xv;
   double sg;
-  if (!skip_v && v_view(X, want, xv, sg, lx, false)) any |= contract(ws, alpha * X.cv * sg, xv, lx, B, lb, C, lc);
+  if (!skip_v) {
+    if (v_view(X, want, xv, sg, lx, false))
+      any |= contract(ws, alpha * X.cv * sg, xv, lx, B, lb, C, lc);
+    else
+      v_slabs(X, want, [&](const View& v) { any |= contract(ws, alpha * X.cv, v, lx, B, lb, C, lc); });
+  }
   if (X.W && X.cw != 0.0)
     for (int herm = 0; herm < 2; ++herm) any |= contract(ws, alpha * X.cw, w_place(*X.W, herm), lx, B, lb, C, lc);
   return any;
@@ -710,7 +738,10 @@ bool contract_x2_left(Workspace& ws, double alpha, const View& A, const char* la
   x2_request(lx, L, want);
   View xv;
   double sg;
-  if (v_view(X, want, xv, sg, lx, false)) any |= contract(ws, alpha * X.cv * sg, A, la, xv, lx, C, lc);
+  if (v_view(X, want, xv, sg, lx, false))
+    any |= contract(ws, alpha * X.cv * sg, A, la, xv, lx, C, lc);
+  else
+    v_slabs(X, want, [&](const View& v) { any |= contract(ws, alpha * X.cv, A, la, v, lx, C, lc); });
   if (X.W && X.cw != 0.0)
     for (int herm = 0; herm < 2; ++herm) any |= contract(ws, alpha * X.cw, A, la, w_place(*X.W, herm), lx, C, lc);
   return any;
@@ -721,7 +752,10 @@ void dot_x2(Workspace& ws, double alpha, const Op2& X, const Tensor& U) {
     if (U.v.iv[k].empty()) return;
   View xv;
   double sg;
-  if (v_view(X, U.v.iv, xv, sg, "scalar term", false)) dot(ws, alpha * X.cv * sg, xv, "pqrs", U.v, "pqrs");
+  if (v_view(X, U.v.iv, xv, sg, "scalar term", false))
+    dot(ws, alpha * X.cv * sg, xv, "pqrs", U.v, "pqrs");
+  else
+    v_slabs(X, U.v.iv, [&](const View& v) { dot(ws, alpha * X.cv, v, "pqrs", U.v, "pqrs"); });
   if (X.W && X.cw != 0.0)
     for (int herm = 0; herm < 2; ++herm) dot(ws, alpha * X.cw, w_place(*X.W, herm), "pqrs", U.v, "pqrs");
 }
@@ -731,7 +765,10 @@ void fetch_x2(Workspace& ws, double alpha, const Op2& X, Tensor& out) {
     if (out.v.iv[k].empty()) return;
   View xv;
   double sg;
-  if (v_view(X, out.v.iv, xv, sg, "materialised class", false)) axpy(ws, alpha * X.cv * sg, xv, "abcd", out, "abcd");
+  if (v_view(X, out.v.iv, xv, sg, "materialised class", false))
+    axpy(ws, alpha * X.cv * sg, xv, "abcd", out, "abcd");
+  else
+    v_slabs(X, out.v.iv, [&](const View& v) { axpy(ws, alpha * X.cv, v, "abcd", out, "abcd"); });
   if (X.W && X.cw != 0.0)
     for (int herm = 0; herm < 2; ++herm) axpy(ws, alpha * X.cw, w_place(*X.W, herm), "abcd", out, "abcd");
 }

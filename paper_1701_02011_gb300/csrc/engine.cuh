@@ -9,6 +9,7 @@
 // that are identically zero are tracked by a bit mask and skipped.
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -146,6 +147,11 @@ void dot(Workspace& ws, double alpha, const View& A, const char* la, const View&
 // other class is served as a permuted view with a sign.
 struct Sym2 {
   std::vector<Tensor> cls;
+  // Classes too large to keep: V on any four intervals is built on demand,
+  // in slabs along the first slot of at most max_elems doubles of working
+  // memory each (nullptr: every class a term needs is stored).
+  std::function<Tensor(const Iv*)> make;
+  long long max_elems = 0;
   bool resolve(const Iv* want, View& out, double& sign) const;
 };
 

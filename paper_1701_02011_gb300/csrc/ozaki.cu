@@ -753,7 +753,7 @@ struct OzChoice {
 void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoice& ch) {
   if (g0.M <= 0 || g0.N <= 0 || g0.K <= 0) return;
   if (g0.nbatch != 1) throw std::runtime_error("split-precision contraction needs nbatch == 1");
-  if (S < 1 || S > kOzakiMaxSlices) throw std::runtime_error("split-precision slices must be 1..7");
+  if (S < 1 || S > kOzakiMaxSlices) throw std::runtime_error("split-precision slices must be 1..8");
   if (!ozaki_supported(g0)) throw std::runtime_error("split-precision contraction too large for 32-bit packing");
   // orient so that the longer output side runs along the 128-row A tiles:
   // C^T = B^T A^T just exchanges the roles of the operands
@@ -880,7 +880,8 @@ void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoic
     case 4: k_ozaki_digits<4><<<g2, PACK_T, 0, st>>>(pd); break;
     case 5: k_ozaki_digits<5><<<g2, PACK_T, 0, st>>>(pd); break;
     case 6: k_ozaki_digits<6><<<g2, PACK_T, 0, st>>>(pd); break;
-    default: k_ozaki_digits<7><<<g2, PACK_T, 0, st>>>(pd); break;
+    case 7: k_ozaki_digits<7><<<g2, PACK_T, 0, st>>>(pd); break;
+    default: k_ozaki_digits<8><<<g2, PACK_T, 0, st>>>(pd); break;
   }
   ws.end(r);
   ws.launches += 1;  // two pack kernels (begin() counted one; the memset is not a kernel)
@@ -1024,7 +1025,7 @@ extern "C" int dsrg_split_gemm(long long M, long long N, long long K, const doub
   using namespace dsrg;
   if (M < 0 || N < 0 || K < 0 || M >= (1LL << 31) || N >= (1LL << 31) || K >= (1LL << 31))
     return set_error(DSRG_ERR_ARG, "split gemm: sizes must be in [0, 2^31)");
-  if (slices < 1 || slices > kOzakiMaxSlices) return set_error(DSRG_ERR_ARG, "split gemm: slices must be 1..7");
+  if (slices < 1 || slices > kOzakiMaxSlices) return set_error(DSRG_ERR_ARG, "split gemm: slices must be 1..8");
   if (M == 0 || N == 0 || K == 0) return DSRG_OK;
   if (!A || !B || !C) return set_error(DSRG_ERR_ARG, "split gemm: NULL pointer");
   cudaStream_t st = (cudaStream_t)stream;

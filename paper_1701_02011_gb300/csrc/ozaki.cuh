@@ -11,13 +11,14 @@
 // kind::f16.  The pairs (t,u) of one level c = t + u are accumulated
 // together (still exact), levels c <= S + 1 are kept, and each level sum is
 // added into a float-float (two FP32) running sum in tensor memory.  The
-// result carries about 7 S bits relative to the row/column maxima.
+// result carries about 7 S bits relative to the row/column maxima.  S <= 8
+// keeps every level sum exact: 8 pairs x 64 x 127^2 < 2^24.
 #pragma once
 #include "engine.cuh"
 
 namespace dsrg {
 
-constexpr int kOzakiMaxSlices = 7;
+constexpr int kOzakiMaxSlices = 8;
 
 // Error status of the split-precision kernels (device flag set when a bounded
 // wait runs out; flag nullptr: the file-scope flag); 0 = ok.  Synchronises st.
