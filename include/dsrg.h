@@ -229,7 +229,10 @@ int dsrg_split_gemm(long long M, long long N, long long K, const double *A, long
  *   "O1" [2p][2h], "O2" [2p][2p][2h][2h]       excitation blocks of
  *                                              1/2 [Htilde(1), A(1)]_{1,2}
  * Spin blocks that change the number of alpha electrons are zero (the library
- * does not store them and fills them in on the copy).
+ * does not store them and fills them in on the copy).  O1 and O2 are kept
+ * only while one [P,P,H,H] tensor takes at most 1 GiB (stored blocks);
+ * beyond that they are folded into Htilde(2) and released, and fetching
+ * them returns DSRG_ERR_STATE.
  * Returns DSRG_ERR_ARG for an unknown name or a wrong count.
  */
 int dsrg_fetch(const dsrg_handle *h, const char *name, double *dst, long long count);

@@ -410,18 +410,27 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   contract_x2(ws, 1.0, X2, "qirs", T1.v, "pi", C2, "pqrs");
   contract_x2(ws, -1.0, X2, "pirs", T1.v, "qi", C2, "pqrs");
   // [X2, T2] one-body with three single contractions
-  Tensor Dee = dress(h, dress(h, T2, 0, e), 1, e);
-  Tensor Ehh = dress(h, dress(h, T2, 2, g), 3, g);
-  Tensor Nhh = dress(h, dress(h, T2, 2, e), 3, e);
+  // dressed copies of T2, one chain at a time (each dressed in place after
+  // its first copy), so that at most one is alive: [P,P,H,H] tensors set
+  // the memory peak of the large instances
   {
-    Tensor D1 = dress(h, Dee, 2, g);
+    Tensor D1 = dress(h, dress(h, dress(h, T2, 0, e), 1, e), 2, g);
     contract_x2(ws, -0.5, X2, "pqrs", D1.v, "rsqj", C1, "pj");
-    Tensor Dgg = dress(h, dress(h, T2, 0, g), 1, g);
-    Tensor D2 = dress(h, Dgg, 2, e);
+  }
+  {
+    Tensor D2 = dress(h, dress(h, dress(h, T2, 0, g), 1, g), 2, e);
     contract_x2(ws, -0.5, X2, "pqrs", D2.v, "rsqj", C1, "pj");
-    Tensor D3 = dress(h, Ehh, 0, e);
+  }
+  {
+    Tensor Ehh = dress(h, dress(h, T2, 2, g), 3, g);
+    contract_x2(ws, 0.5, X2, "pqrs", Ehh.v, "abpq", C2, "abrs");  // hole ladder
+    Tensor D3 = dress(h, std::move(Ehh), 0, e);
     contract_x2(ws, -0.5, X2, "pqrs", D3.v, "rbpq", C1, "bs");
-    Tensor D4 = dress(h, Nhh, 0, g);
+  }
+  {
+    Tensor Nhh = dress(h, dress(h, T2, 2, e), 3, e);
+    contract_x2(ws, -0.5, X2, "pqrs", Nhh.v, "abpq", C2, "abrs");  // hole ladder
+    Tensor D4 = dress(h, std::move(Nhh), 0, g);
     contract_x2(ws, -0.5, X2, "pqrs", D4.v, "rbpq", C1, "bs");
   }
   // [X2, T2] one-body with a two-body cumulant
@@ -484,9 +493,6 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     Tensor gT2 = dress(h, T2, 0, g);
     contract_x2(ws, -1.0, X2, "pqrb", gT2.v, "rbij", C2, "pqij");
   }
-  // hole ladder
-  contract_x2(ws, 0.5, X2, "pqrs", Ehh.v, "abpq", C2, "abrs");
-  contract_x2(ws, -0.5, X2, "pqrs", Nhh.v, "abpq", C2, "abrs");
   // ring: K[x,y,u,w] = sum_{i,a} (Xbar - Xtilde)[x,i,a,w] T2[a,y,i,u], antisymmetrised.
   // X2 is taken piece by piece (V, then W and its Hermitian image on their
   // own boxes) so that no work is spent where a piece vanishes.
@@ -498,9 +504,11 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     Iv kiv[4] = {xi, isect(P, C2.v.iv[1]), isect(H, C2.v.iv[2]), wi};
     Tensor K = make_tensor(ws, 4, kiv, true);
     auto ring_piece = [&](const Tensor& Xs) {
-      Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
+      {
+        Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
+        contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+      }
       Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
-      contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
       contract(ws, -1.0, Xt.v, "xiaw", T2.v, "ayiu", K, "xyuw");
     };
     if (X2.V && X2.cv != 0.0) {
@@ -595,9 +603,8 @@ void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const 
   Tensor Dee = dress(h, dress(h, T2, 0, e), 1, e);
   {
     Tensor D = dress(h, dress(h, Dee, 2, g), 3, g);
-    Iv t[4] = {H, H, P, P};
-    Tensor Dt = make_tensor(ws, 4, t, true);
-    axpy(ws, 1.0, D.v, "rspq", Dt, "pqrs");
+    const int perm[4] = {2, 3, 0, 1};
+    Tensor Dt = alias_permuted(D, perm);  // Dt[p,q,r,s] = D[r,s,p,q], no copy
     dot_x2(ws, 0.25, X2, Dt);
   }
   if (h.na > 0) {
@@ -688,6 +695,22 @@ void issue_energy(Handle& h, bool pt3) {
   ws.tag = "second-order";
   Tensor U1, U2, V1, V2;
   amplitudes(h, &O1, O2, U1, U2, V1, V2);
+  // Htilde(2)_{1,2} excitation blocks = [H0, A(2)] + O - [W, A(1)] / 6,
+  // accumulated in place of [H0, A(2)] (not needed otherwise); O is kept for
+  // dsrg_fetch only while a [P,P,H,H] tensor is small
+  Tensor Z1 = std::move(V1), Z2 = std::move(V2);
+  axpy(ws, 1.0, O1.v, "ai", Z1, "ai");
+  axpy(ws, 1.0, O2.v, "abij", Z2, "abij");
+  const bool keep_o = O2.n * sizeof(double) <= (size_t)1 << 30;
+  if (keep_o) {
+    h.O1 = std::move(O1);
+    h.O2 = std::move(O2);
+  } else {
+    O1.release();
+    O2.release();
+    h.O1.release();
+    h.O2.release();
+  }
   // [W, A(1)]_{1,2}
   ws.tag = "Q";
   Tensor Q1, Q2;
@@ -696,13 +719,8 @@ void issue_energy(Handle& h, bool pt3) {
     Op1Pieces pc = op1_pieces(h, 0.0, &W1, 1.0);
     commutator_A(h, Y1, Op2{nullptr, 0.0, &W2, 1.0}, t1, t2, Q1, Q2, false, &pc);
   }
-  // Htilde(2)_{1,2} excitation blocks = [H0, A(2)] + O - [W, A(1)] / 6,
-  // accumulated in place of [H0, A(2)] (not needed otherwise)
   ws.tag = "Z";
-  Tensor Z1 = std::move(V1), Z2 = std::move(V2);
-  axpy(ws, 1.0, O1.v, "ai", Z1, "ai");
   axpy(ws, -1.0 / 6.0, Q1.v, "ai", Z1, "ai");
-  axpy(ws, 1.0, O2.v, "abij", Z2, "abij");
   axpy(ws, -1.0 / 6.0, Q2.v, "abij", Z2, "abij");
   Q1.release();
   Q2.release();
@@ -715,8 +733,6 @@ void issue_energy(Handle& h, bool pt3) {
   h.res[4] = ws.nresults;
   h.T1b = std::move(U1);
   h.T2b = std::move(U2);
-  h.O1 = std::move(O1);
-  h.O2 = std::move(O2);
   h.launches = ws.launches;
   ws.tag = "";
 }

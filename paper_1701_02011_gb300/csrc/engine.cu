@@ -117,6 +117,9 @@ void Workspace::prof_collect() {
     ev_pool.push_back(r.b);
   }
   recs.clear();
+  if (top && atoi(top) > 0)
+    fprintf(stderr, "[dsrg] peak device memory %.3f GB, reached in step %s\n", peak_ / 1e9,
+            peak_tag_ ? peak_tag_ : "");
 }
 
 namespace {
@@ -266,7 +269,10 @@ double* Workspace::get(size_t n, size_t& cap) {
     }
   }
   in_use_ += got * sizeof(double);
-  peak_ = std::max(peak_, in_use_);
+  if (in_use_ > peak_) {
+    peak_ = in_use_;
+    peak_tag_ = tag;
+  }
   cap = got;
   return p;
 }

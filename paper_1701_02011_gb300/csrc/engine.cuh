@@ -110,6 +110,7 @@ class Workspace {
   struct Blk { double* p; size_t n; };
   std::vector<Blk> free_;
   size_t in_use_ = 0, peak_ = 0;
+  const char* peak_tag_ = "";  // step being issued when the peak was reached
 };
 
 // Names the step issued while it is in scope (restores the outer name).
