@@ -517,10 +517,11 @@ def main(argv=None):
                     help="skip timing the other precision (quick runs, profiler launch lists)")
     ap.add_argument("--no-tune", action="store_true",
                     help="fixed tile/split rules for the split products (default: tuned in the first warm-up)")
-    ap.add_argument("--workload", choices=("cas66_c10_v100_q400", "cas88_c30_v300_q1200", "scan32"),
+    ap.add_argument("--workload", choices=("cas66_c10_v100_q400", "cas88_c30_v300_q1200", "cas44_c40_v500_q1800",
+                                           "scan32"),
                     default=WORKLOAD,
-                    help="the CAS(6,6) instance (default), the CAS(8,8)/300-virtual instance (use "
-                         "--slices 8), or the batched 32-point scan")
+                    help="the CAS(6,6) instance (default), the CAS(8,8)/300-virtual or CAS(4,4)/500-virtual "
+                         "instances (use --slices 8), or the batched 32-point scan")
     ap.add_argument("--scan-budget-gb", type=float, default=120.0,
                     help="device memory per scan batch (handles keep their captured buffers)")
     args = ap.parse_args(argv)
