@@ -421,9 +421,9 @@ def run_scan(args, rank, world, local_rank):
 
     def est_bytes(inst):
         # device footprint of one energy: the stored [P,P,P,H] class of V plus
-        # about twenty [P,P,H,H] tensors, six spin blocks each
+        # about fifteen [P,P,H,H] tensors, six spin blocks each
         p, h = inst["na"] + inst["nv"], inst["nc"] + inst["na"]
-        return 48.0 * p ** 3 * h + 20 * 48.0 * p * p * h * h + 3e8
+        return 48.0 * p ** 3 * h + 15 * 48.0 * p * p * h * h + 3e8
 
     groups, cur, used = [], [], 0.0
     for k in sorted(range(len(insts)), key=lambda k: -est_bytes(insts[k])):
@@ -438,17 +438,33 @@ def run_scan(args, rank, world, local_rank):
 
     def timed(prec, slices, steps):
         """Per batch: handles, one call that warms up and captures, then the
-        timed replays; the batch's handles are freed before the next batch."""
+        timed replays; the batch's handles are freed before the next batch.
+        A batch that runs out of device memory is halved and retried."""
         energies = [None] * len(insts)
         tot = [0.0] * steps
         launches = peak = 0
-        for grp in groups:
+        todo = list(groups)
+        done = []
+        while todo:
+            grp = todo.pop(0)
             devs = [{k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
                      for k, v in insts[i].items()} for i in grp]
             streams = [torch.cuda.Stream() for _ in devs]
             hs = [g.Dsrg(d, stream=st.cuda_stream, precision=prec, slices=slices,
                          tune=(not args.no_tune) and prec == g.DSRG_PREC_SPLIT) for d, st in zip(devs, streams)]
-            e = g.dsrg_pt3_batch(hs)  # eager warm-up, capture, first replay
+            try:
+                e = g.dsrg_pt3_batch(hs)  # eager warm-up, capture, first replay
+            except g.DsrgError as err:
+                for h in hs:
+                    h.close()
+                del devs
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+                if err.code != g.DSRG_ERR_OOM or len(grp) == 1:
+                    raise
+                todo[:0] = [grp[: len(grp) // 2], grp[len(grp) // 2:]]
+                continue
+            done.append(len(grp))
             for _ in range(max(args.warmup - 1, 0)):
                 e = g.dsrg_pt3_batch(hs)
             for s in range(steps):
@@ -468,28 +484,28 @@ def run_scan(args, rank, world, local_rank):
             del devs
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
-        return energies, tot, launches, peak
+        return energies, tot, launches, peak, done
 
     clocks = ClockSampler(local_rank)
     clocks.start()
-    e_split, ts, launches, peak = timed(g.DSRG_PREC_SPLIT, args.slices, args.steps)
+    e_split, ts, launches, peak, batches = timed(g.DSRG_PREC_SPLIT, args.slices, args.steps)
     clk = clocks.stop()
     total_s = max_over_ranks(dist, sum(ts))
     value, tmax = aggregate([total_s], args.steps * len(points), world)
     cmp = None
     if not args.no_comparison:
-        e64, ts64, _, peak64 = timed(g.DSRG_PREC_FP64, 0, 1)
+        e64, ts64, _, peak64, batches64 = timed(g.DSRG_PREC_FP64, 0, 1)
         errs = {k: max(abs(a[k] - b[k]) for a, b in zip(e_split, e64)) for k in ("e2", "e3a", "e3b", "e3")}
         cmp = {"precision": "fp64", "s_per_scan": statistics.median(ts64),
                "value": len(points) / statistics.median(ts64), "max_abs_headline_minus_comparison_Eh": errs,
-               "peak_bytes": peak64}
+               "peak_bytes": peak64, "batches": batches64}
     line = {
         "metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split bf16 tensor-core products)",
         "data": "synthetic (seeded; see DESIGN.md)",
         "config": {"workload": "scan32", "instances": 32, "per_rank": len(points), "precision": "split",
-                   "slices": args.slices, "batches": [len(gp) for gp in groups], "tuned": not args.no_tune,
+                   "slices": args.slices, "batches": batches, "tuned": not args.no_tune,
                    "graph": "one CUDA graph per instance, a batch's graphs replayed concurrently",
                    "l2": "flushed (256 MiB write) before each timed batch"},
         "note": "a step evaluates every scan point of the rank: one batched call per memory batch, host-synchronous",
@@ -522,7 +538,7 @@ def main(argv=None):
                     default=WORKLOAD,
                     help="the CAS(6,6) instance (default), the CAS(8,8)/300-virtual or CAS(4,4)/500-virtual "
                          "instances (use --slices 8), or the batched 32-point scan")
-    ap.add_argument("--scan-budget-gb", type=float, default=120.0,
+    ap.add_argument("--scan-budget-gb", type=float, default=250.0,
                     help="device memory per scan batch (handles keep their captured buffers)")
     args = ap.parse_args(argv)
     rank, world, local_rank = rank_env()

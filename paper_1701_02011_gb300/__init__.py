@@ -23,6 +23,7 @@ DSRG_MEM_HOST = 0
 DSRG_MEM_DEVICE = 1
 DSRG_PREC_FP64 = 0
 DSRG_PREC_SPLIT = 1
+DSRG_ERR_ARG, DSRG_ERR_OOM, DSRG_ERR_CUDA, DSRG_ERR_STATE, DSRG_ERR_INTERNAL = -1, -2, -3, -4, -5
 
 _P = ctypes.POINTER(ctypes.c_double)
 
