@@ -40,13 +40,43 @@ FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
 def _measured_bf16():
+    """bf16 dense peak for a kernel timed inside a long step: the measured
+    sustained figure (the burst figure only if no sustained one is given),
+    else the fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
-        return float(json.load(open(path))["bf16_tflops"])
-    return 1900.0  # fallback figure
+        d = json.load(open(path))
+        if "bf16_tflops_sustained" in d:
+            return float(d["bf16_tflops_sustained"]), "of measured bf16 sustained"
+        return float(d["bf16_tflops"]), "of measured bf16 burst"
+    return 1700.0, "of fallback bf16 sustained"
 
 
-MEASURED_BF16 = _measured_bf16()
+MEASURED_BF16, MEASURED_BF16_SOURCE = _measured_bf16()
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu launch list of
+    the split path on `workload` (profiles/launches_split_<workload>.md: one
+    energy, dram__bytes_read.sum + dram__bytes_write.sum), or None."""
+    path = os.path.join(ROOT, "profiles", f"launches_split_{workload}.md")
+    if not os.path.exists(path):
+        return None, None
+    prefix = {"k_ozaki_mma": ("k_ozaki_mma<",), "k_gemm<0>": ("k_gemm_flat<", "k_gemm<64, 64, 0>")}.get(kernel)
+    if not prefix:
+        return None, None
+    launches = gb = 0.0
+    for line in open(path):
+        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 5 and cells[0].startswith(prefix):
+            try:
+                launches += float(cells[1])
+                gb += float(cells[4])
+            except ValueError:
+                pass
+    if not launches:
+        return None, None
+    return gb * 1e9 / launches, f"profiles/launches_split_{workload}.md (per-launch mean over one energy)"
+
 SAMPLE_WORKLOAD = "cas44_c2_v12_q60"
 
 
@@ -334,9 +364,11 @@ def run_ours(args, rank, world, local_rank):
     tensor_kernel = dom_name == "k_ozaki_mma"
     peak = MEASURED_BF16 if tensor_kernel else FP64_ALU_PEAK_TFLOPS
     achieved = alg / (dom["ms"] / 1000.0) / 1e12 if dom["ms"] > 0 else 0.0
+    traffic, traffic_src = profiled_traffic(dom_name, wl) if args.precision == "split" else (None, None)
     roofline = {"kernel": dom_name, "bound": "tensor" if tensor_kernel else "alu", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "of measured bf16 burst" if tensor_kernel else
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch", "traffic_source": traffic_src,
+                "peak_source": MEASURED_BF16_SOURCE if tensor_kernel else
                 "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz",
                 "algorithmic": note, "launches_per_step": dom["launches"],
                 "avg_launch_ms": dom["ms"] / max(1, dom["launches"]),
