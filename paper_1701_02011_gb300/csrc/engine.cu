@@ -3,9 +3,12 @@
 #include "ozaki.cuh"
 
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <stdexcept>
 
 namespace dsrg {
@@ -123,12 +126,64 @@ void Workspace::prof_collect() {
 }
 
 namespace {
+void run_gemm_fp64(Workspace& ws, const GemmArgs& g0, int kind);
+
+// With ws.tune, a contraction of 5e6 .. 5e7 flops goes to whichever path
+// was faster when its (M, N, K, slices) shape was first met: both timed on
+// the caller's operands with alpha = 0 (C keeps its values), decision cached
+// per device for the process.  Never timed while the stream is captured.
+bool split_faster(Workspace& ws, const GemmArgs& g) {
+  static std::mutex mu;
+  static std::map<std::array<long long, 5>, bool> cache;
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  const std::array<long long, 5> key{g.M, g.N, g.K, (long long)ws.slices, (long long)dev};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  check_cuda(cudaStreamIsCapturing(ws.stream, &cs), "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) return false;
+  GemmArgs gz = g;
+  gz.alpha = 0.0;
+  const bool prof = ws.profiling;
+  const long long launches = ws.launches;
+  ws.profiling = false;
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+  check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+  float ms[2] = {0.f, 0.f};
+  for (int path = 0; path < 2; ++path) {
+    for (int rep = 0; rep < 2; ++rep) {  // the second run is timed
+      check_cuda(cudaEventRecord(e0, ws.stream), "cudaEventRecord");
+      if (path == 0) run_gemm_fp64(ws, gz, K_GEMM);
+      else ozaki_gemm(ws, gz, ws.slices, (int)K_OZAKI_MMA);
+      check_cuda(cudaEventRecord(e1, ws.stream), "cudaEventRecord");
+    }
+    check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    check_cuda(cudaEventElapsedTime(&ms[path], e0, e1), "cudaEventElapsedTime");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ws.profiling = prof;
+  ws.launches = launches;
+  const bool split = ms[1] < ms[0];
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = split;
+  return split;
+}
+
 // split-precision tensor-core path for every contraction with enough work
 // to pay for the operand slicing (about 40 us on the FP64 units); narrow
 // outputs use 32-column tiles, short ones split k over CTAs
-bool split_route(const Workspace& ws, const GemmArgs& g) {
-  return ws.slices > 0 && g.nbatch == 1 && g.K >= 32 && 2.0 * (double)g.M * (double)g.N * (double)g.K >= 5e7 &&
-         ozaki_supported(g);
+bool split_route(Workspace& ws, const GemmArgs& g) {
+  if (!(ws.slices > 0 && g.nbatch == 1 && g.K >= 32 && ozaki_supported(g))) return false;
+  const double fl = 2.0 * (double)g.M * (double)g.N * (double)g.K;
+  if (fl >= 5e7) return true;
+  if (!ws.tune || fl < 5e6 || !g.A || !g.B || !g.C) return false;
+  return split_faster(ws, g);
 }
 
 // one flat launch over the output blocks of tab (npairs operand pairs)
@@ -157,6 +212,11 @@ void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
     ozaki_gemm(ws, g0, ws.slices, kind == K_GEMM ? (int)K_OZAKI_MMA : kind);
     return;
   }
+  run_gemm_fp64(ws, g0, kind);
+}
+
+namespace {
+void run_gemm_fp64(Workspace& ws, const GemmArgs& g0, int kind) {
   if (kind == K_GEMM && gemm_use_flat(g0)) {
     FlatTable tab{};
     tab.a[0] = g0.A;
@@ -223,6 +283,7 @@ void run_gemm(Workspace& ws, const GemmArgs& g0, int kind) {
   if (g.splits > 1) ws.launches++;  // the split-K reduction
   if (part) ws.put(part, cap);  // stream order keeps later reuse behind the reduction
 }
+}  // namespace
 
 void run_axpy(Workspace& ws, const NdArgs& g, double alpha, const double* A, double* C) {
   if (g.total <= 0) return;
@@ -500,6 +561,9 @@ bool contract(Workspace& ws, double alpha, const View& A, const char* la, const 
     C.v.mask |= 1ULL << bc;
   }
   if (pairs.empty()) return false;
+  g.A = a.p + pairs[0].oa;  // operands of the first spin block: timing data for the route choice
+  g.B = b.p + pairs[0].ob;
+  g.C = c.p + pairs[0].oc;
   if (!split_route(ws, g) && gemm_use_flat(g)) {
     // all spin blocks in flat launches: pairs that share an output block are
     // summed inside one thread, so no two CTAs of a launch write the same C
