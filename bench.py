@@ -75,7 +75,8 @@ def profiled_traffic(kernel, workload):
                 pass
     if not launches:
         return None, None
-    return gb * 1e9 / launches, f"profiles/launches_split_{workload}.md (per-launch mean over one energy)"
+    return gb * 1e9 / launches, (f"profiles/launches_split_{workload}.md (per-launch mean over one energy of the "
+                                 "--no-tune run: under ncu's serialised launches the tuner's timings are skewed)")
 
 SAMPLE_WORKLOAD = "cas44_c2_v12_q60"
 
