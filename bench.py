@@ -427,6 +427,30 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def scan_point_bytes(inst):
+    """Device footprint of one energy of a scan point: the stored [P,P,P,H]
+    class of V plus about fifteen [P,P,H,H] tensors, six spin blocks each."""
+    p, h = inst["na"] + inst["nv"], inst["nc"] + inst["na"]
+    return 48.0 * p ** 3 * h + 15 * 48.0 * p * p * h * h + 3e8
+
+
+def scan_groups(insts, budget_bytes):
+    """Indices of the points grouped into batches whose estimated footprints
+    add up to at most budget_bytes (largest points first; a point larger than
+    the budget gets a batch of its own)."""
+    groups, cur, used = [], [], 0.0
+    for k in sorted(range(len(insts)), key=lambda k: -scan_point_bytes(insts[k])):
+        b = scan_point_bytes(insts[k])
+        if cur and used + b > budget_bytes:
+            groups.append(cur)
+            cur, used = [], 0.0
+        cur.append(k)
+        used += b
+    if cur:
+        groups.append(cur)
+    return groups
+
+
 def run_scan(args, rank, world, local_rank):
     """The 32-point scan of uneven instances (core 4-12, CAS(4,4) or CAS(6,6),
     virtual 60-200, auxiliary 4 x virtual, virtual gap shrinking along the
@@ -452,22 +476,7 @@ def run_scan(args, rank, world, local_rank):
     insts = [synth.scan_instance(j) for j in points]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def est_bytes(inst):
-        # device footprint of one energy: the stored [P,P,P,H] class of V plus
-        # about fifteen [P,P,H,H] tensors, six spin blocks each
-        p, h = inst["na"] + inst["nv"], inst["nc"] + inst["na"]
-        return 48.0 * p ** 3 * h + 15 * 48.0 * p * p * h * h + 3e8
-
-    groups, cur, used = [], [], 0.0
-    for k in sorted(range(len(insts)), key=lambda k: -est_bytes(insts[k])):
-        b = est_bytes(insts[k])
-        if cur and used + b > args.scan_budget_gb * 1e9:
-            groups.append(cur)
-            cur, used = [], 0.0
-        cur.append(k)
-        used += b
-    if cur:
-        groups.append(cur)
+    groups = scan_groups(insts, args.scan_budget_gb * 1e9)
 
     def timed(prec, slices, steps):
         """Per batch: handles, one call that warms up and captures, then the

@@ -261,16 +261,24 @@ def config_instance(name: str, **kw) -> dict:
     return make_instance(**c)
 
 
-def scan_instance(j: int, nscan: int = 32) -> dict:
-    """Instance j of a 32-point dissociation-like scan: uneven sizes, the
-    virtual band's lower edge falls linearly from 0.6 to 0.05 Eh."""
+def scan_sizes(j: int, nscan: int = 32) -> dict:
+    """Sizes of point j of the 32-point scan (drawn first, from their own
+    seed): core uniform {4..12}, CAS(4,4) or CAS(6,6), virtual uniform
+    {60..200}, aux 4 x virtual, virtual lower edge 0.6 -> 0.05 Eh."""
     rng = np.random.default_rng(SEED0 + 100 + j)
     nc = int(rng.integers(4, 13))
     cas = 4 if rng.random() < 0.5 else 6
     nv = int(rng.integers(60, 201))
     vlo = 0.6 - 0.55 * j / (nscan - 1)
-    return make_instance(nc, cas, cas, nv, 4 * nv, 0.5, seed=SEED0 + 1000 + j,
-                         eps_vir=(vlo, 5.0))
+    return {"nc": nc, "na": cas, "nv": nv, "naux": 4 * nv, "vlo": vlo}
+
+
+def scan_instance(j: int, nscan: int = 32) -> dict:
+    """Instance j of a 32-point dissociation-like scan: uneven sizes, the
+    virtual band's lower edge falls linearly from 0.6 to 0.05 Eh."""
+    z = scan_sizes(j, nscan)
+    return make_instance(z["nc"], z["na"], z["na"], z["nv"], z["naux"], 0.5, seed=SEED0 + 1000 + j,
+                         eps_vir=(z["vlo"], 5.0))
 
 
 def random_small(nc, na, nel, nv, naux, s=0.5, seed=1):

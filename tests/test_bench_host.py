@@ -55,3 +55,16 @@ def test_aggregate_single_rank():
     v, t = bench.aggregate([2.0], 4, 1)
     assert (v, t) == (2.0, 2.0)
     assert bench.instance_seed_offset(0) == 0 and bench.instance_seed_offset(3) == 3000
+
+
+def test_scan_groups_cover_every_point_within_budget():
+    insts = [synth.scan_sizes(j) for j in range(32)]
+    sizes = [bench.scan_point_bytes(i) for i in insts]
+    for budget in (3e11, 1.2e11, 4e10, 1.0):
+        groups = bench.scan_groups(insts, budget)
+        flat = sorted(k for g in groups for k in g)
+        assert flat == list(range(32))  # every point exactly once
+        for g in groups:
+            assert len(g) == 1 or sum(sizes[k] for k in g) <= budget
+    assert len(bench.scan_groups(insts, 3e11)) == 1
+    assert all(len(g) == 1 for g in bench.scan_groups(insts, 1.0))

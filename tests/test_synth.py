@@ -89,3 +89,21 @@ def test_instances_are_deterministic():
     for k in ("eps", "B", "l3aab"):
         assert np.array_equal(a[k], b[k])
     assert np.allclose(a["B"], np.transpose(a["B"], (0, 2, 1)))
+
+
+def test_scan_recipe():
+    """The 32-point scan: core 4..12, CAS(4,4) or CAS(6,6), virtual 60..200,
+    aux = 4 x virtual, and the virtual band's lower edge falling linearly
+    from 0.6 to 0.05 Eh along the scan (shrinking gaps, as in dissociation)."""
+    sizes = [synth.scan_sizes(j) for j in range(32)]
+    for j, z in enumerate(sizes):
+        assert 4 <= z["nc"] <= 12 and z["na"] in (4, 6) and 60 <= z["nv"] <= 200
+        assert z["naux"] == 4 * z["nv"]
+        assert abs(z["vlo"] - (0.6 - 0.55 * j / 31)) < 1e-12
+    assert len({(z["nc"], z["nv"]) for z in sizes}) > 20  # uneven sizes
+    for j in (0, 31):  # two full instances: sizes and the virtual band
+        inst = synth.scan_instance(j)
+        z = sizes[j]
+        assert (inst["nc"], inst["na"], inst["nv"], inst["naux"]) == (z["nc"], z["na"], z["nv"], z["naux"])
+        eps_v = np.asarray(inst["eps"])[z["nc"] + z["na"]:]
+        assert eps_v.min() >= z["vlo"] - 1e-12 and eps_v.max() <= 5.0
