@@ -455,6 +455,26 @@ __global__ void k_ozaki_reduce(const OzArgs a) {
   }
 }
 
+// The same sum with one warp per output element, for many splits over few
+// outputs (one thread would chain hundreds of dependent loads): lane l adds
+// z = l, l + 32, ... in order, then a fixed shuffle tree combines the lanes.
+template <int BN>
+__global__ void k_ozaki_reduce_warp(const OzArgs a) {
+  const long long Mp = (long long)a.MT * OZ_BM, ldp = (long long)a.NT * BN;
+  const long long total = a.M * a.N;
+  const int lane = threadIdx.x & 31;
+  const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = wid; i < total; i += nw) {
+    const long long m = i / a.N, n = i - m * a.N;
+    double s = 0.0;
+    for (int z = lane; z < a.splits; z += 32) s += a.part[((long long)z * Mp + m) * ldp + n];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) a.C[c_offset(m, a.nM, a.eM, a.cM) + c_offset(n, a.nN, a.eN, a.cN)] += a.alpha * s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // operand preparation
 // ---------------------------------------------------------------------------
@@ -714,7 +734,13 @@ void oz_launch_bn(const OzArgs& a, int MT, int NT, cudaStream_t st) {
   if (smem < 120 * 1024) smem = 120 * 1024;
   oz_smem_attribute<BN>();
   k_ozaki_mma<BN><<<dim3(MT, NT, a.splits > 1 ? a.splits : 1), OZ_THREADS, smem, st>>>(a);
-  if (a.splits > 1) k_ozaki_reduce<BN><<<oz_grid(a.M * a.N), 256, 0, st>>>(a);
+  if (a.splits > 1) {
+    // few outputs, many splits: a warp per output keeps loads in flight
+    if (a.splits >= 32 && a.M * a.N < 152LL * 256)
+      k_ozaki_reduce_warp<BN><<<oz_grid(a.M * a.N * 32), 256, 0, st>>>(a);
+    else
+      k_ozaki_reduce<BN><<<oz_grid(a.M * a.N), 256, 0, st>>>(a);
+  }
 }
 
 void oz_launch_mma(const OzArgs& a, int MT, int NT, int BN, cudaStream_t st) {
