@@ -9,7 +9,7 @@ workload below, through the library's C interface.
 Workload (default): 10 core, CAS(6,6) reference (400 Ms=0 determinants,
 seeded random CI vector with exact gamma1 / lambda2 / lambda3), 100 virtual,
 400 auxiliary functions, s = 0.5 Eh^-2; orbital energies and B^Q_pq drawn as
-described in the design doc.  Inputs are smaller than L2, so L2 is flushed
+drawn from the seeded generator in synth/.  Inputs are smaller than L2, so L2 is flushed
 (a 256 MiB write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -398,7 +398,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (split bf16 tensor-core products)",
-        "data": "synthetic (seeded; see DESIGN.md)",
+        "data": "synthetic (seeded: uniform orbital energies per block, symmetric Gaussian B^Q scaled by 0.1 exp(-3Q/naux), random CAS CI vector with exact cumulants)",
         "config": dict(config_dict(inst, args.precision, wl), slices=args.slices if args.precision == "split" else None,
                        tuned=(not args.no_tune) and args.precision == "split"),
         "effective_tflops_ladder_build": eff_tflops,
@@ -545,7 +545,7 @@ def run_scan(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split bf16 tensor-core products)",
-        "data": "synthetic (seeded; see DESIGN.md)",
+        "data": "synthetic (seeded: uniform orbital energies per block, symmetric Gaussian B^Q scaled by 0.1 exp(-3Q/naux), random CAS CI vector with exact cumulants)",
         "config": {"workload": "scan32", "instances": 32, "per_rank": len(points), "precision": "split",
                    "slices": args.slices, "batches": batches, "tuned": not args.no_tune,
                    "graph": "one CUDA graph per instance, a batch's graphs replayed concurrently",

@@ -36,6 +36,9 @@ extern "C" {
 #define DSRG_ERR_CUDA (-3)    /* CUDA runtime or launch error                */
 #define DSRG_ERR_STATE (-4)   /* call out of order (e.g. NULL handle)        */
 #define DSRG_ERR_INTERNAL (-5)
+#define DSRG_ERR_TIMEOUT (-6) /* a bounded wait inside a kernel ran out; the
+                                 kernel released its resources and returned,
+                                 the results of the call are not valid       */
 
 #define DSRG_MEM_HOST 0   /* input pointers are host memory; copied at load     */
 #define DSRG_MEM_DEVICE 1 /* input pointers are device memory on the current GPU;
@@ -92,6 +95,13 @@ typedef struct {
                      alpha = 0, so nothing changes) and keeps the fastest;
                      0 = fixed rules.  Results differ from the fixed rules
                      only in summation order.  No counterpart in the paper. */
+  long long wait_limit; /* budget, in SM clock cycles, of every bounded wait
+                     inside the split-precision kernel (on copies and
+                     tensor-core products it issued itself); 0 selects 2^32
+                     (about 2 s).  When a wait runs out the kernel stops
+                     work, waits for what it has in flight, frees its tensor
+                     memory and the call returns DSRG_ERR_TIMEOUT.  Negative
+                     values are DSRG_ERR_ARG.  No counterpart in the paper. */
 } dsrg_options;
 
 typedef struct {
@@ -183,19 +193,23 @@ int dsrg_df_ladder(int n, int naux, int p0, int np, int nh, const double *B, con
                    void *stream);
 
 /*
- * dsrg_df_ladder without any device allocation (no counterpart in the paper:
- * it serves callers that cannot call cudaMalloc, e.g. code running during
- * CUDA stream capture or inside a framework that owns all device memory).
- * Same arguments, contraction and result as dsrg_df_ladder.  The (pr|qs)
- * rows live in one fixed file-scope device array of 2^22 doubles (32 MiB)
- * that every GPU on which the library's device code is loaded holds until
- * the process exits, so np^3 <= 2^22 (np <= 161) is required; larger np
- * returns DSRG_ERR_ARG with a message.  The first call on a device looks up
- * that array's device address (with the device current); make that first
- * call before any stream capture.  All calls share the array and it keeps
- * the last call's contents (each batch clears what it accumulates into);
- * calls that overlap on the GPU (other streams, other host threads) race on
- * it and must be serialised by the caller.  Synchronises `stream`.
+ * dsrg_df_ladder without any device allocation.  No counterpart in the
+ * paper: it serves callers that may not call cudaMalloc, such as frameworks
+ * whose caching allocator reserved the device memory up front (a library
+ * allocation would fail or fragment their pool) and embedded or real-time
+ * runtimes that forbid allocation after start-up.  Same arguments,
+ * contraction and result as dsrg_df_ladder; no cudaMalloc, cudaFree or
+ * allocating library routine is called.  The (pr|qs) rows live in one fixed
+ * file-scope device array of 2^22 doubles (32 MiB) that every GPU on which
+ * the library's device code is loaded holds until the process exits, so
+ * np^3 <= 2^22 (np <= 161) is required; larger np returns DSRG_ERR_ARG with
+ * a message.  Set-up: the first call on a device (and the first call after
+ * that device's context changed, e.g. after cudaDeviceReset) looks up the
+ * array's device address with the device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (each batch clears what it accumulates into); calls
+ * that overlap on the GPU (other streams, other host threads) race on it and
+ * must be serialised by the caller.  Synchronises `stream`.
  */
 int dsrg_df_ladder_noalloc(int n, int naux, int p0, int np, int nh, const double *B, const double *t, double *L,
                            void *stream);
@@ -212,8 +226,9 @@ int dsrg_df_ladder_noalloc(int n, int naux, int p0, int np, int nh, const double
  * so the result carries about 7*slices bits relative to the product of the
  * row and column maxima (Ozaki et al., Numer. Algorithms 59 (2012) 95).
  * Scratch is allocated and released inside the call; synchronises `stream`.
- * Errors: DSRG_ERR_ARG (sizes >= 2^31, slices, NULL), DSRG_ERR_CUDA (launch
- * failure, or a bounded wait inside the kernel ran out).
+ * Errors: DSRG_ERR_ARG (sizes >= 2^31, slices, NULL), DSRG_ERR_OOM (scratch),
+ * DSRG_ERR_CUDA (launch failure), DSRG_ERR_TIMEOUT (a bounded wait inside the
+ * kernel ran out, default budget).
  */
 int dsrg_split_gemm(long long M, long long N, long long K, const double *A, long long lda, const double *B,
                     long long ldb, double *C, long long ldc, double alpha, int slices, void *stream);

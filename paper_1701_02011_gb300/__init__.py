@@ -23,7 +23,7 @@ DSRG_MEM_HOST = 0
 DSRG_MEM_DEVICE = 1
 DSRG_PREC_FP64 = 0
 DSRG_PREC_SPLIT = 1
-DSRG_ERR_ARG, DSRG_ERR_OOM, DSRG_ERR_CUDA, DSRG_ERR_STATE, DSRG_ERR_INTERNAL = -1, -2, -3, -4, -5
+DSRG_ERR_ARG, DSRG_ERR_OOM, DSRG_ERR_CUDA, DSRG_ERR_STATE, DSRG_ERR_INTERNAL, DSRG_ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
 
 _P = ctypes.POINTER(ctypes.c_double)
 
@@ -37,7 +37,7 @@ class dsrg_inputs(ctypes.Structure):
 
 class dsrg_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("slices", ctypes.c_int),
-                ("tune", ctypes.c_int)]
+                ("tune", ctypes.c_int), ("wait_limit", ctypes.c_longlong)]
 
 
 class dsrg_energies(ctypes.Structure):
@@ -149,10 +149,11 @@ def make_inputs(inst: dict):
 
 
 def dsrg_init(inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0,
-              tune: bool = False) -> ctypes.c_void_p:
+              tune: bool = False, wait_limit: int = 0) -> ctypes.c_void_p:
     L = load_library()
     s, keep = make_inputs(inst)
-    opt = dsrg_options(precision, ctypes.c_void_p(stream) if stream else None, int(slices), int(bool(tune)))
+    opt = dsrg_options(precision, ctypes.c_void_p(stream) if stream else None, int(slices), int(bool(tune)),
+                       int(wait_limit))
     h = ctypes.c_void_p()
     _check(L.dsrg_init(ctypes.byref(s), ctypes.byref(opt), ctypes.byref(h)))
     return h
@@ -258,8 +259,9 @@ def dsrg_df_ladder(B, t, L, p0: int, stream=None) -> None:
 
 
 def dsrg_df_ladder_noalloc(B, t, L, p0: int, stream=None) -> None:
-    """dsrg_df_ladder without device allocation (fixed 32 MiB scratch, np <= 161);
-    for callers that cannot allocate, e.g. during stream capture."""
+    """dsrg_df_ladder without device allocation (fixed 32 MiB scratch, np <= 161),
+    for callers whose device memory is owned by their own allocator or that may
+    not allocate after start-up; overlapping calls must be serialised."""
     naux, n, _ = B.shape
     np_, _, nh, _ = t.shape
     _check(load_library().dsrg_df_ladder_noalloc(n, naux, p0, np_, nh, _dev_ptr(B), _dev_ptr(t), _dev_ptr(L),
@@ -283,9 +285,11 @@ def dsrg_split_gemm(A, B, C, alpha: float = 1.0, slices: int = 6, stream=None) -
 class Dsrg:
     """Convenience owner of one handle."""
 
-    def __init__(self, inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0, tune: bool = False):
+    def __init__(self, inst: dict, stream=None, precision=DSRG_PREC_FP64, slices: int = 0, tune: bool = False,
+                 wait_limit: int = 0):
         self.sizes = (int(inst["nc"]), int(inst["na"]), int(inst["nv"]))
-        self.h = dsrg_init(inst, stream, precision, slices, tune)
+        self.h = None
+        self.h = dsrg_init(inst, stream, precision, slices, tune, wait_limit)
 
     def load(self, inst):
         dsrg_load(self.h, inst)

@@ -21,11 +21,10 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+// the DSRG_ERR_* code an exception stands for (the code it carries)
 int classify(const std::exception& e) {
-  std::string m = e.what();
-  if (m.find("cudaMalloc") != std::string::npos || m.find("out of memory") != std::string::npos)
-    return DSRG_ERR_OOM;
-  if (m.find("CUDA") != std::string::npos || m.find("cuda") != std::string::npos) return DSRG_ERR_CUDA;
+  if (const auto* d = dynamic_cast<const dsrg::Error*>(&e)) return d->code;
+  if (dynamic_cast<const std::bad_alloc*>(&e)) return DSRG_ERR_OOM;
   return DSRG_ERR_INTERNAL;
 }
 
@@ -152,6 +151,7 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
     slices = opts->slices ? opts->slices : 6;
     if (slices < 1 || slices > 8) return fail(DSRG_ERR_ARG, "slices must be 1..8");
   }
+  if (opts && opts->wait_limit < 0) return fail(DSRG_ERR_ARG, "wait_limit must be >= 0");
   cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
   bool own = false;
   if (!st) {
@@ -167,6 +167,7 @@ int dsrg_init(const dsrg_inputs* in, const dsrg_options* opts, dsrg_handle** out
   h->own_stream = own;
   h->ws.slices = slices;
   h->ws.tune = opts && opts->tune != 0;
+  h->ws.wait_cycles = opts ? opts->wait_limit : 0;
   try {
     h->nc = in->nc;
     h->na = in->na;
@@ -241,7 +242,7 @@ void reset_status(dsrg::Handle& h) {
 void check_status(dsrg::Handle& h) {
   dsrg::check_cuda(cudaGetLastError(), "kernel launch");
   if (h.ws.slices > 0 && dsrg::ozaki_status(h.stream, h.ws.oz_status))
-    throw std::runtime_error("CUDA: a bounded wait in the split-precision kernel ran out");
+    throw dsrg::Error(DSRG_ERR_TIMEOUT, "a bounded wait in the split-precision kernel ran out");
 }
 
 void eager_energy(dsrg::Handle& h, bool pt3, dsrg_energies* out) {

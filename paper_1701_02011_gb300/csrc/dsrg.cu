@@ -642,6 +642,15 @@ void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const 
   }
 }
 
+// E(2), E3a, E3b from their result slots, into the last three slots
+static void sum_components(Handle& h) {
+  Workspace& ws = h.ws;
+  if (ws.nresults > ws.cap_results - 3) throw std::runtime_error("out of result slots");
+  int r = ws.begin(K_DOT, 0.0, 8.0 * (double)ws.nresults);
+  launch_sum_slots(ws.results, h.res, ws.results + ws.cap_results - 3, ws.stream);
+  ws.end(r);
+}
+
 // Every kernel and copy of one energy, enqueued on the handle's stream with
 // no host synchronisation (so that it can be captured in a CUDA graph); the
 // result-slot ranges of E(2), E3a, E3b go to h.res.
@@ -677,6 +686,7 @@ void issue_energy(Handle& h, bool pt3) {
   h.T1 = std::move(T1);
   h.T2 = std::move(T2);
   if (!pt3) {
+    sum_components(h);
     h.launches = ws.launches;
     ws.tag = "";
     return;
@@ -733,29 +743,22 @@ void issue_energy(Handle& h, bool pt3) {
   h.res[4] = ws.nresults;
   h.T1b = std::move(U1);
   h.T2b = std::move(U2);
+  sum_components(h);
   h.launches = ws.launches;
   ws.tag = "";
 }
 
-static double sum_slots(const std::vector<double>& v, int lo, int hi) {
-  long double t = 0.0L;
-  for (int i = lo; i < hi; ++i) t += v[i];
-  return (double)t;
-}
-
-// One copy of the result slots of the last issued energy, summed on the host
-// (long double) per component.  Synchronises the stream.
+// One copy of the three energy components, reduced on the device from the
+// result slots of the last issued energy.  Synchronises the stream.
 void finish_energy(Handle& h, double* e2, double* e3a, double* e3b) {
-  const int n = h.res[4];
-  std::vector<double> v((size_t)(n > 0 ? n : 0));
-  h.d2h_bytes = (long long)n * (long long)sizeof(double);
-  if (n > 0)
-    check_cuda(cudaMemcpyAsync(v.data(), h.ws.results, n * sizeof(double), cudaMemcpyDeviceToHost, h.ws.stream),
-               "copy results");
+  double v[3] = {0.0, 0.0, 0.0};
+  h.d2h_bytes = (long long)sizeof v;
+  check_cuda(cudaMemcpyAsync(v, h.ws.results + h.ws.cap_results - 3, sizeof v, cudaMemcpyDeviceToHost, h.ws.stream),
+             "copy results");
   check_cuda(cudaStreamSynchronize(h.ws.stream), "sync");
-  *e2 = sum_slots(v, h.res[0], h.res[1]);
-  *e3a = h.res_pt3 ? sum_slots(v, h.res[2], h.res[3]) : 0.0;
-  *e3b = h.res_pt3 ? sum_slots(v, h.res[3], h.res[4]) : 0.0;
+  *e2 = v[0];
+  *e3a = h.res_pt3 ? v[1] : 0.0;
+  *e3b = h.res_pt3 ? v[2] : 0.0;
 }
 
 void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b) {

@@ -14,7 +14,9 @@
 namespace dsrg {
 
 void check_cuda(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    throw Error(e == cudaErrorMemoryAllocation ? DSRG_ERR_OOM : DSRG_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 View View::sub(const Iv* want) const {
@@ -677,7 +679,7 @@ void dot(Workspace& ws, double alpha, const View& A, const char* la, const View&
   DotBlocks blk{};
   auto flush = [&]() {
     if (blk.n == 0) return;
-    if (ws.nresults >= ws.cap_results) throw std::runtime_error("out of result slots");
+    if (ws.nresults >= ws.cap_results - 3) throw std::runtime_error("out of result slots");  // last 3: the sums
     int r = ws.nresults++;
     int rec = ws.begin(K_DOT, 2.0 * (double)g.total * blk.n, 16.0 * (double)g.total * blk.n);
     launch_dot_blocks(g, alpha, blk, ws.dot_scratch, ws.dot_scratch_len, ws.dot_ticket, ws.results + r, ws.stream);

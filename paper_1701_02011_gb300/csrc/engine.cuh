@@ -10,12 +10,23 @@
 #pragma once
 #include <cstdint>
 #include <functional>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
+#include "../../include/dsrg.h"
 #include "kernels.cuh"
 
 namespace dsrg {
+
+// Exception carrying the DSRG_ERR_* code the C interface returns for it:
+// CUDA errors (DSRG_ERR_CUDA, or DSRG_ERR_OOM for a failed allocation),
+// DSRG_ERR_TIMEOUT for a bounded wait that ran out.  Other exceptions map
+// to DSRG_ERR_INTERNAL.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
 
 struct Iv {
   int lo = 0, hi = 0;
@@ -86,6 +97,7 @@ class Workspace {
   int dot_scratch_len = 0;
   unsigned* dot_ticket = nullptr;  // zero between launches
   int* oz_status = nullptr;        // split-precision kernels' error flag (device; nullptr: file-scope flag)
+  long long wait_cycles = 0;       // budget of the split kernels' bounded waits (0: default)
   bool tune = false;               // time tile/split candidates of new split-product shapes
   unsigned long long generation = 0;  // bumped when cached blocks are freed (captured graphs go stale)
   long long launches = 0;

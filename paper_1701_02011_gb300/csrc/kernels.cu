@@ -560,6 +560,26 @@ __global__ void __launch_bounds__(DOT_THREADS) k_dot_blocks(const NdArgs g, cons
   }
 }
 
+// Final reduction of the energy components: out[c] = sum of slots
+// [r[c], r[c+1]) for c = 0, 1, 2, each in a fixed order with a double-double
+// running sum (Knuth's two-sum), one thread per component.
+__global__ void k_sum_slots(const double* __restrict__ slots, int r0, int r1, int r2, int r3, int r4,
+                            double* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c >= 3) return;
+  const int lo = c == 0 ? r0 : c == 1 ? r2 : r3;
+  const int hi = c == 0 ? r1 : c == 1 ? r3 : r4;
+  double s = 0.0, e = 0.0;
+  for (int i = lo; i < hi; ++i) {
+    const double x = slots[i];
+    const double t = s + x;
+    const double bp = t - s;
+    e += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  out[c] = s + e;
+}
+
 __global__ void k_add_diagonal(double* D, int n, double v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) D[(long long)i * n + i] += v;
 }
@@ -869,6 +889,10 @@ void launch_dot_blocks(const NdArgs& g0, double alpha, const DotBlocks& p, doubl
   const dim3 grid((unsigned)gx, (unsigned)p.n);
   if (nd_prepare(g)) k_dot_blocks<true><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
   else k_dot_blocks<false><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
+}
+
+void launch_sum_slots(const double* slots, const int* r, double* out, cudaStream_t st) {
+  k_sum_slots<<<1, 32, 0, st>>>(slots, r[0], r[1], r[2], r[3], r[4], out);
 }
 
 void launch_add_diagonal(double* D, int n, double v, cudaStream_t st) {

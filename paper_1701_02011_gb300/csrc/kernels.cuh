@@ -134,6 +134,9 @@ void launch_gemm_flat(const GemmArgs& g, const FlatPlan& p, const FlatTable& tab
 // kind 0: generic contraction, 1: DF build of (pr|qs), 2: ladder contraction
 void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind = 0);
 void launch_fill(double* p, long long n, double v, cudaStream_t st);
+// out[0] = sum slots[r0, r1), out[1] = sum slots[r2, r3), out[2] = sum
+// slots[r3, r4): compensated, fixed order (the energy components E(2), E3a, E3b)
+void launch_sum_slots(const double* slots, const int* r, double* out, cudaStream_t st);
 // D[i][i] += v for the n x n row-major D
 void launch_add_diagonal(double* D, int n, double v, cudaStream_t st);
 

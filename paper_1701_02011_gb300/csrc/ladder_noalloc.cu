@@ -1,11 +1,13 @@
 // A variant of dsrg_df_ladder for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at the point where they need the
-// ladder: code running while a CUDA stream is being captured into a graph,
-// allocators that own all device memory up front (a framework's caching
-// pool), or embedded runtimes that forbid allocation after start-up.  This
-// entry point takes inputs and outputs from the caller and keeps its own
-// scratch in a fixed, file-scope device array instead.
+// Some callers may not call cudaMalloc at the point where they need the
+// ladder: frameworks whose caching allocator reserved all device memory up
+// front (a cudaMalloc from inside a library would fail or fragment their
+// pool), and embedded or real-time runtimes that forbid allocation after
+// start-up.  This entry point takes inputs and outputs from the caller and
+// keeps its own scratch in a fixed, file-scope device array instead.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -22,10 +24,43 @@ static __device__ __align__(256) double g_ladder_scratch[kScratchDoubles];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
+
+// The current context's process-unique id, through driver entry points the
+// runtime hands out (the library does not link the driver library itself).
+// 0 if the driver cannot tell.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+    return id;
+  return 0;
+}
 
 // Host code cannot use g_ladder_scratch directly: its name here denotes a
-// host-side shadow, not device memory.  Look up the device address once per
-// device, with that device current.
+// host-side shadow, not device memory.  The device address is looked up at
+// set-up, once per device with that device current, and again whenever the
+// device's context has changed since (after cudaDeviceReset the module is
+// loaded anew and the array may sit elsewhere).  The runtime creates the
+// context on the first runtime call, so the id is read after the lookup.
 int scratch_address(double** out, std::string& msg) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -38,14 +73,17 @@ int scratch_address(double** out, std::string& msg) {
     return DSRG_ERR_ARG;
   }
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  const unsigned long long ctx = g_addr[dev] ? current_context_id() : 0;
+  if (!g_addr[dev] || ctx == 0 || ctx != g_ctx_id[dev]) {
     double* p = nullptr;
     e = cudaGetSymbolAddress((void**)&p, g_ladder_scratch);
     if (e != cudaSuccess || !p) {
       msg = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      g_addr[dev] = nullptr;
       return DSRG_ERR_CUDA;
     }
     g_addr[dev] = p;
+    g_ctx_id[dev] = current_context_id();
   }
   *out = g_addr[dev];
   return DSRG_OK;

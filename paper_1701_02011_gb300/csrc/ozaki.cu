@@ -20,7 +20,10 @@ constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // A tile: 8192 bf16 = 16 KiB
 constexpr int OZ_TILE_BYTES = OZ_TILE_ELEMS * 2;
 // exponents are stored as 2048 + frexp exponent of the row / column maximum (0: all zero)
 constexpr unsigned OZ_EBIAS = 2048;
-constexpr long long OZ_WAIT_LIMIT = 1LL << 22;
+// default budget of a bounded wait, and the fixed budget of the waits that
+// drain copies and products in flight after a wait ran out (SM clock cycles,
+// about 2 s at 2 GHz)
+constexpr long long OZ_WAIT_CYCLES = 1LL << 32;
 
 __device__ int g_oz_status;
 
@@ -59,11 +62,26 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// bounded wait: false if the phase did not complete in time
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  for (long long i = 0; i < OZ_WAIT_LIMIT; ++i)
+// non-blocking test of the phase
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false if the phase did not complete within `budget` SM clock
+// cycles (tested once without blocking, then polled with try_wait)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long long budget) {
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_test(bar, phase)) return true;
+    if (clock64() - t0 > budget) return false;
     if (mbar_try(bar, phase)) return true;
-  return false;
+  }
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -138,6 +156,7 @@ struct OzArgs {
   long long cM[4], cN[4];
   int rowfast;  // C's row index has the smaller stride (epilogue writes along rows)
   int* status;
+  long long wait_cycles;  // budget of each bounded wait (clock cycles)
   // split over k tiles: CTA z covers [z*ktper, (z+1)*ktper) and writes its
   // scaled partial tile to part[z][MT*128][NT*BN] instead of C
   int splits, ktper;
@@ -300,7 +319,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     load_pending = true;
   }
   for (int kt = kt0; kt < kt1 && ok; ++kt) {
-    ok = mbar_wait(&bar_load, ph_load);
+    ok = mbar_wait(&bar_load, ph_load, a.wait_cycles);
     if (ok) ph_load ^= 1;  // a timed-out wait keeps its parity for the second wait
     if (tid == 0 && ok) load_pending = false;
     ok = __syncthreads_and(ok) != 0;
@@ -313,7 +332,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     for (int c = 2; c <= L; ++c) {
       // level c complete; start level c + 1 in the other accumulator (folded
       // before the last barrier), or, after the last level, the next k tile
-      bool w = mbar_wait(&bar_mma[c & 1], ph_mma[c & 1]);
+      bool w = mbar_wait(&bar_mma[c & 1], ph_mma[c & 1], a.wait_cycles);
       if (w) ph_mma[c & 1] ^= 1;
       if (tid == 0 && w) mma_pending[c & 1] = false;
       ok = __syncthreads_and(w) != 0;
@@ -364,11 +383,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     }
   }
   // after a timed-out wait: give the copies and MMAs still in flight a second
-  // bounded wait before the shared memory and TMEM are released
+  // bounded wait (the fixed default budget) before the shared memory and TMEM
+  // are released
   if (!ok && tid == 0) {
-    if (load_pending) mbar_wait(&bar_load, ph_load);
+    if (load_pending) mbar_wait(&bar_load, ph_load, OZ_WAIT_CYCLES);
     for (int i = 0; i < 2; ++i)
-      if (mma_pending[i]) mbar_wait(&bar_mma[i], ph_mma[i]);
+      if (mma_pending[i]) mbar_wait(&bar_mma[i], ph_mma[i], OZ_WAIT_CYCLES);
   }
   // epilogue: the scaled tile 2^(ea[m] + fb[n]) (hi + lo) goes to shared
   // memory (the operand tiles are free once the last MMA has completed; rows
@@ -924,6 +944,7 @@ void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoic
   a.alpha = g0.alpha;
   a.C = g0.C;
   a.status = ws.oz_status;
+  a.wait_cycles = ws.wait_cycles > 0 ? ws.wait_cycles : OZ_WAIT_CYCLES;
   a.splits = splits;
   a.ktper = ktper;
   a.part = part;
@@ -1083,9 +1104,12 @@ extern "C" int dsrg_split_gemm(long long M, long long N, long long K, const doub
     g.nbatch = 1;
     ozaki_gemm(ws, g, slices, K_OZAKI_MMA);
     check_cuda(cudaGetLastError(), "split gemm launch");
-    if (ozaki_status(st, nullptr)) return set_error(DSRG_ERR_CUDA, "split gemm: a bounded wait in the kernel ran out");
+    if (ozaki_status(st, nullptr))
+      return set_error(DSRG_ERR_TIMEOUT, "split gemm: a bounded wait in the kernel ran out");
+  } catch (const Error& e) {
+    return set_error(e.code, e.what());
   } catch (const std::exception& e) {
-    return set_error(DSRG_ERR_CUDA, e.what());
+    return set_error(DSRG_ERR_INTERNAL, e.what());
   }
   return DSRG_OK;
 }

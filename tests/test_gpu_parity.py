@@ -48,10 +48,10 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=[str(s) for s in SHAPES])
-def test_energies_and_intermediates(lib, shape):
-    nc, na, nel, nv, naux = shape
-    inst = synth.make_instance(nc, na, nel, nv, naux, 0.5, seed=sum(shape) + 7)
+def _check_against_oracle(lib, inst):
+    """Energies within TOL_E; T1, T2, second-order T1, T2 and the excitation
+    blocks of 1/2 [Htilde(1), A(1)]_{1,2} element by element."""
+    nc, na = inst["nc"], inst["na"]
     ref = dsrg.dsrg_pt3(inst, return_intermediates=True)
     P, I = ref["_problem"], ref["_inter"]
     h = lib.Dsrg(inst)
@@ -80,6 +80,34 @@ def test_energies_and_intermediates(lib, shape):
         assert np.abs((g2 - w2)[m2]).max(initial=0.0) < 1e-11 * max(1.0, np.abs(w2).max())
     finally:
         h.close()
+    return ref
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[str(s) for s in SHAPES])
+def test_energies_and_intermediates(lib, shape):
+    nc, na, nel, nv, naux = shape
+    _check_against_oracle(lib, synth.make_instance(nc, na, nel, nv, naux, 0.5, seed=sum(shape) + 7))
+
+
+def test_degenerate_and_near_degenerate_denominators(lib):
+    """Orbital energies with exact and near degeneracies across blocks, so that
+    many denominators D of Eqs. T1_1st, T2_1st, T1_2nd and T2_2nd are exactly
+    0 (regulariser limit 0) or 1e-9 .. 1e-6 (the series branch and the switch
+    point s D^2 = 1e-12), on both sides."""
+    inst = synth.make_instance(2, 4, 4, 6, 24, 0.5, seed=41)
+    eps = inst["eps"].copy()
+    nc, na = 2, 4
+    a0, v0 = nc, nc + na
+    eps[0], eps[1] = -3.0, -2.5            # exactly representable sums
+    eps[v0 + 0] = eps[a0 + 0]               # D = 0: T1[v0, u0], T2[v0, x, u0, x], ...
+    eps[v0 + 1] = eps[a0 + 1] + 1e-8        # |D| ~ 1e-8: series branch
+    eps[v0 + 2] = eps[a0 + 2] - 3e-9
+    eps[v0 + 3] = eps[a0 + 3] + 1e-6 / np.sqrt(0.5)   # s D^2 at the 1e-12 switch
+    eps[v0 + 4], eps[v0 + 5] = -6.75, 1.25  # eps_c0 + eps_c1 = eps_v4 + eps_v5: D = 0 for T2[v4, v5, c0, c1]
+    inst["eps"] = eps
+    ref = _check_against_oracle(lib, inst)
+    D2 = ref["_problem"].D2
+    assert (np.abs(D2) == 0.0).sum() > 0 and ((np.abs(D2) > 0) & (np.abs(D2) < 1e-7)).sum() > 0
 
 
 def test_pt2_call_matches_pt3_e2(lib):

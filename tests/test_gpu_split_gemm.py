@@ -60,3 +60,22 @@ def test_tile_shapes_orientation_and_k_split(lib, M, N, K):
     C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
     lib.dsrg_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 1.0, 1)
     assert np.array_equal(C.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("slices,lo,hi", [(2, 1e-10, 2.0 ** -10), (3, 1e-12, 2.0 ** -17)])
+def test_few_slices_truncate_visibly(lib, slices, lo, hi):
+    """With 2 or 3 digit slices the product carries about 7 S bits relative to
+    the row/column maxima: its error against FP64 must exceed FP64 rounding by
+    orders of magnitude (so an FP64 fallback would fail here) and stay within
+    the digit-truncation bound."""
+    import torch
+    rng = np.random.default_rng(5)
+    M, N, K = 300, 200, 500
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    ref = A @ B
+    bound = np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
+    C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    lib.dsrg_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 1.0, slices)
+    err = (np.abs(C.cpu().numpy() - ref) / bound).max()
+    assert lo < err < hi, err
