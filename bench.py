@@ -3,16 +3,19 @@
 
 One step = one full unrelaxed DSRG-MRPT3 energy (first-order amplitudes,
 E(2), the second-order transformed Hamiltonian with the density-fitted
-particle-particle ladder, second-order amplitudes, E(3)) of the synthetic
-workload below, through the library's C interface.
+particle-particle ladder, rings and cumulant terms, second-order amplitudes,
+E(3)) of one synthetic instance, through the library's C interface.
 
-Workload (default): 10 core, CAS(6,6) reference (400 Ms=0 determinants,
-seeded random CI vector with exact gamma1 / lambda2 / lambda3), 100 virtual,
-400 auxiliary functions, s = 0.5 Eh^-2; orbital energies and B^Q_pq drawn as
-drawn from the seeded generator in synth/.  Inputs are smaller than L2, so L2 is flushed
-(a 256 MiB write) before every timed step.
+Workload (default): 30 core, CAS(8,8) reference (4900 Ms=0 determinants,
+seeded random CI vector with exact gamma1 / lambda2 / lambda3), 300 virtual,
+1200 auxiliary functions, s = 0.5 Eh^-2, inputs from the seeded generator in
+synth/ (uniform orbital energies per block, symmetric Gaussian B^Q scaled by
+0.1 exp(-3Q/naux)).  Headline: the split-precision path (8 digit slices);
+the FP64 path is timed on one energy beside it and every energy component
+is compared.  The working set (tens of GB) is far larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload cas88_c30_v300_q1200|cas66_c10_v100_q400|cas44_c40_v500_q1800|scan32]
 
 Prints one JSON line on rank 0.  With N > 1 (torchrun) every rank computes
 its own instance (weak scaling, no collective on the data path).
@@ -33,7 +36,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "PT3 energies/sec & effective TFLOP/s: mixed-precision vs FP64 path at ≤1µEh"
-WORKLOAD = "cas66_c10_v100_q400"
+WORKLOAD = "cas88_c30_v300_q1200"
+# digit slices of the split path per workload: enough for 1e-6 Eh on energies
+# of up to 1e4 (6), 1e5 (7) and 1e7 Eh (8)
+SLICES = {"cas66_c10_v100_q400": 6, "cas88_c30_v300_q1200": 8, "cas44_c40_v500_q1800": 8, "scan32": 7}
 # FP64 runs on the SM's FP64 FMA units (no tcgen05 FP64 kind): 152 SMs x
 # 2 FP64 FMA per clock per SM x 2 flop x 2.070 GHz maximum SM clock.
 FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -54,31 +60,26 @@ def _measured_bf16():
 
 MEASURED_BF16, MEASURED_BF16_SOURCE = _measured_bf16()
 
-def profiled_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` from the committed ncu launch list of
-    the split path on `workload` (profiles/launches_split_<workload>.md: one
-    energy, dram__bytes_read.sum + dram__bytes_write.sum), or None."""
-    path = os.path.join(ROOT, "profiles", f"launches_split_{workload}.md")
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the split-precision tensor-core kernel from
+    the committed ncu capture (profiles/k_ozaki_mma_<workload>.md, a line
+    'traffic_bytes_per_launch: B' and the SHA-256 of the kernel source the
+    counters were taken on).  None when absent or when the source changed."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"k_ozaki_mma_{workload}.md")
+    src = os.path.join(ROOT, "paper_1701_02011_gb300", "csrc", "ozaki.cu")
     if not os.path.exists(path):
         return None, None
-    prefix = {"k_ozaki_mma": ("k_ozaki_mma<",), "k_gemm<0>": ("k_gemm_flat<", "k_gemm<64, 64, 0>")}.get(kernel)
-    if not prefix:
-        return None, None
-    launches = gb = 0.0
+    rec = {}
     for line in open(path):
-        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 5 and cells[0].startswith(prefix):
-            try:
-                launches += float(cells[1])
-                gb += float(cells[4])
-            except ValueError:
-                pass
-    if not launches:
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha256")):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip().strip("`")
+    if "traffic_bytes_per_launch" not in rec:
         return None, None
-    return gb * 1e9 / launches, (f"profiles/launches_split_{workload}.md (per-launch mean over one energy of the "
-                                 "--no-tune run: under ncu's serialised launches the tuner's timings are skewed)")
-
-SAMPLE_WORKLOAD = "cas44_c2_v12_q60"
+    if rec.get("kernel_source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+        return None, f"profiles/k_ozaki_mma_{workload}.md predates the current kernel source"
+    return float(rec["traffic_bytes_per_launch"]), f"profiles/k_ozaki_mma_{workload}.md"
 
 
 # ----------------------------------------------------------------------------
@@ -163,68 +164,86 @@ class ClockSampler:
 # CPU oracle timing (the baseline, on a bounded sample)
 # ----------------------------------------------------------------------------
 
-def _nso(inst):
-    return 2 * (inst["nc"] + inst["na"] + inst["nv"])
+def cpu_threads():
+    """Threads the oracle's numpy/BLAS calls may use on this host."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(k, "").isdigit():
+            return int(os.environ[k])
+    return os.cpu_count()
 
 
-def oracle_sample_rate(target_inst, reps: int):
-    """Time the oracle as it stands on the small CAS(4,4) instance and scale
-    by its dense O(n_so^6) cost to the target size.  Returns
-    (energies_per_s at target size, seconds per sample, sample text)."""
-    import synth
-    from oracle import dsrg as odsrg
-    inst = synth.config_instance(SAMPLE_WORKLOAD)
-    times = []
-    for _ in range(reps):
+class OracleSample:
+    """The CPU oracle (oracle.dsrg_df, plain FP64 numpy, as it stands) on a
+    bounded part of the benchmark's own instance: its particle-particle
+    ladder (Eq. scaling_problem, the dominant O(N^6) step of the energy at
+    these sizes), a few spin-orbital output rows at a time, with <pq||rs>
+    built from B^Q for those rows.  A whole oracle energy at this size takes
+    far longer than a benchmark may run.  The energies/s figure counts the
+    ladder alone (every row at the measured time per row) and so is an
+    upper bound on the oracle's rate for whole energies."""
+
+    def __init__(self, inst):
+        from oracle import dsrg_df
         t0 = time.perf_counter()
-        odsrg.dsrg_pt3(inst)
-        times.append(time.perf_counter() - t0)
-    t = statistics.median(times)
-    scale = (_nso(target_inst) / _nso(inst)) ** 6
-    text = (f"full PT3 oracle evaluation of the CAS(4,4), 2 core, 12 virtual, 60 aux instance "
-            f"({_nso(inst)} spin orbitals), median of {reps}, scaled by the oracle's dense O(n_so^6) "
-            f"cost to {_nso(target_inst)} spin orbitals (x{scale:.3g})")
-    return 1.0 / (t * scale), t, text
+        self.s = dsrg_df.LadderSample(inst)
+        self.setup_s = time.perf_counter() - t0
+        self.next = 0
 
+    def step(self, rows):
+        lo = self.next % self.s.nrows
+        hi = min(lo + rows, self.s.nrows)
+        t0 = time.perf_counter()
+        self.s.rows(lo, hi)
+        dt = time.perf_counter() - t0
+        self.next = hi
+        return dt, hi - lo
 
-# ----------------------------------------------------------------------------
-# arms
-# ----------------------------------------------------------------------------
+    def rate(self, seconds, rows):
+        return rows / (seconds * self.s.nrows)
+
+    def text(self, rows_done, seconds):
+        return (f"oracle.dsrg_df particle-particle ladder of this instance, {rows_done} of its {self.s.nrows} "
+                f"spin-orbital output rows in {seconds:.2f} s (first-order amplitudes and eta.eta.T2 formed "
+                f"beforehand in {self.setup_s:.1f} s, not counted); energies/s = rows / (time x all rows): the "
+                f"ladder alone, an upper bound on the oracle's rate for whole energies")
+
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     import synth
-    target = synth.config_instance(WORKLOAD)
+    wl = args.workload if args.workload != "scan32" else WORKLOAD
+    inst = synth.config_instance(wl)
+    smp = OracleSample(inst)
     for _ in range(args.warmup):
-        oracle_sample_rate(target, 1)
-    rates, secs = [], []
-    text = ""
+        smp.step(args.ref_rows)
+    secs, rows = [], 0
     for _ in range(args.steps):
-        r, t, text = oracle_sample_rate(target, 1)
-        rates.append(r)
-        secs.append(t)
-    value = statistics.median(rates)
-    cores = os.cpu_count()
+        dt, nr = smp.step(args.ref_rows)
+        secs.append(dt)
+        rows += nr
+    tot = sum(secs)
+    value = smp.rate(tot, rows)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(target, "fp64 CPU oracle"),
-        "cpu_baseline": {"value": value, "unit": "energies/s", "cores": cores, "kind": "oracle",
-                         "sample": text},
+        "data": "synthetic", "config": config_dict(inst, wl),
+        "cpu_baseline": {"value": value, "unit": "energies/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": smp.text(rows, tot)},
         "e2e": {"value": value, "unit": "energies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": "each step evaluates --ref-rows rows of the oracle's ladder; ms_per_step is that sample's time",
     }
     print(json.dumps(line), flush=True)
 
 
-def config_dict(inst, precision, workload=WORKLOAD):
+def config_dict(inst, workload):
     na = inst["na"]
     from math import comb
     dets = comb(na, na // 2) ** 2
     return {"workload": workload, "nc": inst["nc"], "na": na, "nv": inst["nv"], "naux": inst["naux"],
-            "s": inst["s"], "precision": precision, "l2": "flushed (256 MiB write) before each timed step",
-            "reference": f"CAS({na},{na}) Ms=0, {dets} determinants"}
+            "s": inst["s"], "reference": f"CAS({na},{na}) Ms=0, {dets} determinants",
+            "l2": "inputs and working set larger than L2; L2 also flushed (256 MiB write) before each timed step"}
 
 
 def input_bytes(inst):
@@ -235,16 +254,27 @@ def input_bytes(inst):
     return tot
 
 
-def alg_flops(inst):
-    """Algorithmic flop counts of the dense contractions of one PT3 energy.
-
-    ladder over particle pairs i <= j: h(h+1) p^4; (pr|qs) build with the
-    pair-swap symmetry: Q p^2 (p^2 + 1); p = active + virtual, h = core + active.
-    """
+def alg_flops(inst, steps):
+    """Algorithmic flops of one PT3 energy, fixed before measuring:
+    F_lad = h (h+1) v^4 (spatial ladder over i <= j), F_build = Q v^2 (v^2+1)
+    ((eg|fh) under pair exchange), F_ring = 2 h^3 p^3 k_ring (k_ring = ring
+    products of that shape in the energy's term list), F_low = every other
+    contraction as counted by the library (2 M N K each).  h = core +
+    active, p = active + virtual, v = virtual, Q = auxiliary.  `steps`: the
+    library's per-step FP64 flop counts of a profiled energy."""
     h = inst["nc"] + inst["na"]
     p = inst["na"] + inst["nv"]
-    Q = inst["naux"]
-    return {"ladder": h * (h + 1) * p ** 4, "build": Q * p * p * (p * p + 1)}
+    v, Q = inst["nv"], inst["naux"]
+    f_lad = h * (h + 1) * v ** 4
+    f_build = Q * v * v * (v * v + 1)
+    unit = 2.0 * h ** 3 * p ** 3
+    ring = steps.get("ring", {}).get("flops", 0.0)
+    total = sum(x["flops"] for x in steps.values())
+    counted_ladder = sum(steps.get(k, {}).get("flops", 0.0) for k in ("ladder-build", "ladder-contract"))
+    f_low = total - counted_ladder - ring
+    return {"F_lad": f_lad, "F_build": f_build, "F_ring": ring, "k_ring": ring / unit if unit else 0.0,
+            "F_low": f_low, "F_alg": f_lad + f_build + ring + f_low,
+            "library_counted_total": total, "library_counted_ladder": counted_ladder}
 
 
 def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, clocks=None, tune=False,
@@ -276,8 +306,7 @@ def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, c
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    # one profiled energy: per-kernel device time, launches and flops of a step
-    stats = {}
+    stats, step_stats = {}, {}
     if profile:
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -286,8 +315,9 @@ def _time_path(g, torch, dev, stream, flush, steps, warmup, precision, slices, c
         h.pt3()
         torch.cuda.synchronize()
         stats = h.profile_stats()
+        step_stats = h.profile_steps()
         h.profile(False)
-    return h, ms, energies, stats, launches, clk
+    return h, ms, energies, stats, step_stats, launches, clk
 
 
 def run_ours(args, rank, world, local_rank):
@@ -305,30 +335,24 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     libbuild.build()
     wl = args.workload
+    slices = args.slices or SLICES[wl]
     inst = synth.config_instance(wl, seed=synth.CONFIGS[wl]["seed"] + instance_seed_offset(rank))
     stream = torch.cuda.Stream()
     dev = {k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
            for k, v in inst.items()}
     torch.cuda.synchronize()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    other = "fp64" if args.precision == "split" else "split"
-    # comparison path first (untimed for the headline), then the headline path
-    ms2 = e_other = None
-    if not args.no_comparison:
-        # context and accuracy reference only: one warm-up, one timed energy
-        h2, ms2, e_other, stats2, _, _ = _time_path(g, torch, dev, stream, flush, 1, 1, other, args.slices,
-                                                    tune=not args.no_tune, profile=False)
-        h2.close()
     if dist:
         dist.barrier()
-    h, ms, energies, stats, launches, clocks = _time_path(g, torch, dev, stream, flush, args.steps, args.warmup,
-                                                          args.precision, args.slices, ClockSampler(local_rank),
-                                                          tune=not args.no_tune)
+    h, ms, energies, stats, steps, launches, clocks = _time_path(
+        g, torch, dev, stream, flush, args.steps, args.warmup, args.precision, slices, ClockSampler(local_rank),
+        tune=not args.no_tune)
     if dist:
         dist.barrier()
     total_s = max_over_ranks(dist, sum(ms) / 1000.0)
     value, tmax = aggregate([total_s], args.steps, world)
     ms_per_step = 1000.0 * tmax / args.steps
+    peak_bytes = g.dsrg_peak_bytes(h.h)
     # ---- end to end: host buffers (pinned), copies inside the timed region
     host = {}
     for k, v in inst.items():
@@ -338,7 +362,7 @@ def run_ours(args, rank, world, local_rank):
             host[k] = v
     e2e_ms = []
     d2h = 0
-    for k in range(max(1, min(args.steps, 5))):
+    for k in range(max(1, min(args.steps, args.e2e_steps))):
         with torch.cuda.stream(stream):
             flush.zero_()
         torch.cuda.synchronize()
@@ -347,78 +371,73 @@ def run_ours(args, rank, world, local_rank):
         h.pt3()
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-        d2h = g.dsrg_last_d2h_bytes(h.h) + 32
+        d2h = g.dsrg_last_d2h_bytes(h.h)
     e2e_value = world * 1000.0 / statistics.median(e2e_ms)
     h.close()
+    # ---- the other precision on one energy: speed and per-component accuracy
+    other = "fp64" if args.precision == "split" else "split"
+    cmp = None
+    if not args.no_comparison:
+        torch.cuda.empty_cache()
+        cw = 1 if wl == "cas66_c10_v100_q400" else 0
+        h2, ms2, e_other, _, _, _, _ = _time_path(g, torch, dev, stream, flush, 1, cw, other, slices,
+                                                  tune=not args.no_tune, profile=False)
+        h2.close()
+        diff = {k: energies[k] - e_other[k] for k in ("e2", "e3a", "e3b", "e3")}
+        rel = {k: abs(diff[k]) / max(abs(e_other[k]), 1e-300) for k in diff}
+        cmp = {"precision": other, "ms_per_step": ms2[0], "value": 1000.0 / ms2[0], "warmup": cw,
+               "energies": e_other, "headline_minus_comparison_Eh": diff, "relative": rel,
+               "max_abs_Eh": max(abs(x) for x in diff.values()),
+               "speedup": ms2[0] / ms_per_step if args.precision == "split" else ms_per_step / ms2[0]}
     # ---- roofline of the dominant kernel (by device time in the profiled energy)
     dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
-    af = alg_flops(inst)
     step_s = total_s / args.steps
-    if dom_name == "k_gemm<1>":
-        alg, note = af["build"], "Q p^2 (p^2+1) per energy ((pr|qs) build, pair-swap symmetry)"
-    elif dom_name == "k_gemm<2>":
-        alg, note = af["ladder"], "h (h+1) p^4 per energy (ladder, i <= j)"
-    elif dom_name == "k_ozaki_mma":
-        alg, note = dom["flops"], "executed bf16 flops: 2 x 128-row x tile-width x 64-k tiles x S(S+1)/2 digit pairs"
-    else:
-        alg, note = dom["flops"], "2 M N K summed over the kernel's contractions"
     tensor_kernel = dom_name == "k_ozaki_mma"
     peak = MEASURED_BF16 if tensor_kernel else FP64_ALU_PEAK_TFLOPS
-    achieved = alg / (dom["ms"] / 1000.0) / 1e12 if dom["ms"] > 0 else 0.0
-    traffic, traffic_src = profiled_traffic(dom_name, wl) if args.precision == "split" else (None, None)
+    sec = dom["ms"] / 1000.0
+    achieved = dom["flops"] / sec / 1e12 if sec > 0 else 0.0
+    executed = dom["exec_flops"] / sec / 1e12 if sec > 0 else 0.0
+    traffic, traffic_src = profiled_traffic(wl) if tensor_kernel else (None, None)
     roofline = {"kernel": dom_name, "bound": "tensor" if tensor_kernel else "alu", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_unit": "bytes per launch", "traffic_source": traffic_src,
+                "traffic_unit": "DRAM bytes per launch", "traffic_source": traffic_src,
                 "peak_source": MEASURED_BF16_SOURCE if tensor_kernel else
                 "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz",
-                "algorithmic": note, "launches_per_step": dom["launches"],
-                "avg_launch_ms": dom["ms"] / max(1, dom["launches"]),
-                "share_of_step": (dom["ms"] / 1000.0) / max(step_s, 1e-30)}
-    tensor = stats.get("k_ozaki_mma", {"launches": 0, "ms": 0.0, "flops": 0.0})
-    roof_tensor = None
-    if tensor["launches"] and dom_name != "k_ozaki_mma":
-        executed = tensor["flops"] / (tensor["ms"] / 1000.0) / 1e12
-        roof_tensor = {"kernel": "k_ozaki_mma", "bound": "tensor", "achieved": executed, "peak": MEASURED_BF16,
-                       "unit": "TFLOP/s", "frac": executed / MEASURED_BF16,
-                       "note": "executed bf16 flops (digit-slice pairs and tile padding included) per device time",
-                       "launches_per_step": tensor["launches"],
-                       "share_of_step": (tensor["ms"] / 1000.0) / max(step_s, 1e-30)}
-    fp64k = stats.get("k_gemm<0>", {"launches": 0, "ms": 0.0, "flops": 0.0})
-    roof_fp64 = None
-    if fp64k["launches"] and dom_name != "k_gemm<0>":
-        a64 = fp64k["flops"] / (fp64k["ms"] / 1000.0) / 1e12
-        roof_fp64 = {"kernel": "k_gemm<0>", "bound": "alu", "achieved": a64, "peak": FP64_ALU_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": a64 / FP64_ALU_PEAK_TFLOPS,
-                     "note": "2 M N K of the FP64 contractions per device time",
-                     "launches_per_step": fp64k["launches"],
-                     "share_of_step": (fp64k["ms"] / 1000.0) / max(step_s, 1e-30)}
-    eff_tflops = (af["ladder"] + af["build"]) * value / 1e12
-    err = {k: energies[k] - e_other[k] for k in ("e2", "e3a", "e3b", "e3")} if e_other else None
+                "algorithmic": "FP64 flops of the products the kernel computes (2 M N K each) per device time",
+                "executed_tflops": executed, "executed_frac": executed / peak,
+                "executed_note": "bf16 tensor flops issued: every digit pair (S(S+1)/2) over the padded tiles",
+                "launches_per_step": dom["launches"], "avg_launch_ms": dom["ms"] / max(1, dom["launches"]),
+                "share_of_step": sec / max(step_s, 1e-30)}
+    fl = alg_flops(inst, steps)
+    eff_tflops = fl["F_alg"] * value / world / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "energies/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (split bf16 tensor-core products)",
-        "data": "synthetic (seeded: uniform orbital energies per block, symmetric Gaussian B^Q scaled by 0.1 exp(-3Q/naux), random CAS CI vector with exact cumulants)",
-        "config": dict(config_dict(inst, args.precision, wl), slices=args.slices if args.precision == "split" else None,
+        "data": "synthetic (seeded: uniform orbital energies per block, symmetric Gaussian B^Q scaled by "
+                "0.1 exp(-3Q/naux), random CAS CI vector with exact cumulants)",
+        "config": dict(config_dict(inst, wl), precision=args.precision,
+                       slices=slices if args.precision == "split" else None,
                        tuned=(not args.no_tune) and args.precision == "split"),
-        "effective_tflops_ladder_build": eff_tflops,
-        "energies": energies,
-        "comparison": None if ms2 is None else
-        {"precision": other, "ms_per_step": statistics.median(ms2), "value": 1000.0 / statistics.median(ms2),
-         "energies": e_other, "headline_minus_comparison_Eh": err},
-        "clocks": clocks,
-        "gpu_launches": launches,
+        "effective_tflops": eff_tflops, "flops_per_energy": fl,
+        "energies": energies, "comparison": cmp, "clocks": clocks, "gpu_launches": launches,
         "roofline": roofline,
-        "roofline_tensor": roof_tensor,
-        "roofline_fp64": roof_fp64,
-        "kernels_per_step": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items() if v["launches"]},
+        "kernels_per_step": {k: {"launches": v["launches"], "ms": v["ms"], "flops": v["flops"],
+                                 "exec_flops": v["exec_flops"]} for k, v in stats.items() if v["launches"]},
+        "steps_of_energy_ms": {k: round(v["ms"], 3) for k, v in steps.items()},
+        "peak_device_bytes": peak_bytes,
         "e2e": {"value": e2e_value, "unit": "energies/s", "h2d_bytes_per_step": input_bytes(inst),
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "steps": len(e2e_ms)},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, t, text = oracle_sample_rate(inst, args.cpu_reps)
-        line["cpu_baseline"] = {"value": cb, "unit": "energies/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": text}
+        smp = OracleSample(inst)
+        secs, rows = 0.0, 0
+        while secs < args.cpu_seconds and rows < smp.s.nrows:
+            dt, nr = smp.step(1)
+            secs += dt
+            rows += nr
+        line["cpu_baseline"] = {"value": smp.rate(secs, rows), "unit": "energies/s", "cores": cpu_threads(),
+                                "kind": "oracle", "sample": smp.text(rows, secs)}
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:
@@ -530,7 +549,8 @@ def run_scan(args, rank, world, local_rank):
 
     clocks = ClockSampler(local_rank)
     clocks.start()
-    e_split, ts, launches, peak, batches = timed(g.DSRG_PREC_SPLIT, args.slices, args.steps)
+    slices = args.slices or SLICES["scan32"]
+    e_split, ts, launches, peak, batches = timed(g.DSRG_PREC_SPLIT, slices, args.steps)
     clk = clocks.stop()
     total_s = max_over_ranks(dist, sum(ts))
     value, tmax = aggregate([total_s], args.steps * len(points), world)
@@ -547,7 +567,7 @@ def run_scan(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (split bf16 tensor-core products)",
         "data": "synthetic (seeded: uniform orbital energies per block, symmetric Gaussian B^Q scaled by 0.1 exp(-3Q/naux), random CAS CI vector with exact cumulants)",
         "config": {"workload": "scan32", "instances": 32, "per_rank": len(points), "precision": "split",
-                   "slices": args.slices, "batches": batches, "tuned": not args.no_tune,
+                   "slices": slices, "batches": batches, "tuned": not args.no_tune,
                    "graph": "one CUDA graph per instance, a batch's graphs replayed concurrently",
                    "l2": "flushed (256 MiB write) before each timed batch"},
         "note": "a step evaluates every scan point of the rank: one batched call per memory batch, host-synchronous",
@@ -563,23 +583,25 @@ def run_scan(args, rank, world, local_rank):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--cpu-reps", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="oracle rows timed for the cpu_baseline (at least one row)")
+    ap.add_argument("--ref-rows", type=int, default=1, help="oracle ladder rows per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=("split", "fp64"), default="split",
-                    help="headline path; the other is timed alongside for comparison")
-    ap.add_argument("--slices", type=int, default=6)
+                    help="headline path; the other is timed on one energy alongside for comparison")
+    ap.add_argument("--slices", type=int, default=0, help="digit slices of the split path (0: per workload)")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="end-to-end energies timed (at most --steps)")
     ap.add_argument("--no-comparison", action="store_true",
                     help="skip timing the other precision (quick runs, profiler launch lists)")
     ap.add_argument("--no-tune", action="store_true",
                     help="fixed tile/split rules for the split products (default: tuned in the first warm-up)")
-    ap.add_argument("--workload", choices=("cas66_c10_v100_q400", "cas88_c30_v300_q1200", "cas44_c40_v500_q1800",
-                                           "scan32"),
-                    default=WORKLOAD,
-                    help="the CAS(6,6) instance (default), the CAS(8,8)/300-virtual or CAS(4,4)/500-virtual "
-                         "instances (use --slices 8), or the batched 32-point scan")
+    ap.add_argument("--workload", choices=("cas88_c30_v300_q1200", "cas66_c10_v100_q400", "cas44_c40_v500_q1800",
+                                           "scan32"), default=WORKLOAD,
+                    help="CAS(8,8)/30 core/300 virtual (default), CAS(6,6)/10 core/100 virtual, "
+                         "CAS(4,4)/40 core/500 virtual, or the batched 32-point scan")
     ap.add_argument("--scan-budget-gb", type=float, default=250.0,
                     help="device memory per scan batch (handles keep their captured buffers)")
     args = ap.parse_args(argv)

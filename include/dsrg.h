@@ -157,15 +157,23 @@ long long dsrg_last_launch_count(const dsrg_handle *h);
 /* Per-kernel timing.  dsrg_profile(h, 1) makes later dsrg_pt2/dsrg_pt3 calls
  * bracket every launch of this library with CUDA events on the handle's
  * stream and accumulate, per kernel, the launch count, the summed device
- * time (ms), the executed FP64 flops (2 M N K per contraction) and the bytes
- * moved by elementwise kernels; dsrg_profile(h, 0) stops.  Both reset the
- * totals.  dsrg_profile_stats reads kernel index 0 .. 5 (generic
- * contraction, ladder (pr|qs) build, ladder contraction, axpy, dot,
- * amplitude kernels); *name receives a static string.  DSRG_ERR_ARG past the
- * last index. */
+ * time (ms), the FP64 flops of the contractions it computes (2 M N K each),
+ * the flops it executes (split-precision products: every digit pair over the
+ * padded tiles; FP64 kernels: the same as flops) and the bytes moved by
+ * element-wise kernels; dsrg_profile(h, 0) stops.  Both reset the totals.
+ * dsrg_profile_stats reads kernel index 0 .. 7 (generic FP64 contraction,
+ * FP64 ladder (pr|qs) build, FP64 ladder contraction, axpy, dot, amplitude
+ * kernels, split-precision operand packing, split-precision tensor-core
+ * product); *name receives a static string.  DSRG_ERR_ARG past the last
+ * index.  dsrg_profile_step reads the same launches grouped by the step of
+ * the energy they belong to (first-order amplitudes, ladder build, ladder
+ * contraction, ring, ...), in the order the steps first ran; *name stays
+ * valid until the next profiled call.  No counterpart in the paper. */
 int dsrg_profile(dsrg_handle *h, int enable);
 int dsrg_profile_stats(const dsrg_handle *h, int kernel, const char **name, long long *launches, double *ms,
-                       double *flops, double *bytes);
+                       double *flops, double *exec_flops, double *bytes);
+int dsrg_profile_step(const dsrg_handle *h, int step, const char **name, long long *launches, double *ms,
+                      double *flops);
 
 /* Device-to-host bytes read back by the last dsrg_pt2 / dsrg_pt3 call (the
  * per-block partial sums of the energy components; -1 on a NULL handle). */

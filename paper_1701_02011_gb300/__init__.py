@@ -47,6 +47,7 @@ class dsrg_energies(ctypes.Structure):
 
 EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_pt3_batch", "dsrg_free", "dsrg_last_error",
            "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
+           "dsrg_profile_step",
            "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc", "dsrg_split_gemm")
 
 _lib = None
@@ -84,8 +85,11 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
     L.dsrg_profile.argtypes = [ctypes.c_void_p, ctypes.c_int]
     L.dsrg_profile.restype = ctypes.c_int
     L.dsrg_profile_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
-                                     ctypes.POINTER(ctypes.c_longlong), _P, _P, _P]
+                                     ctypes.POINTER(ctypes.c_longlong), _P, _P, _P, _P]
     L.dsrg_profile_stats.restype = ctypes.c_int
+    L.dsrg_profile_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                    ctypes.POINTER(ctypes.c_longlong), _P, _P]
+    L.dsrg_profile_step.restype = ctypes.c_int
     L.dsrg_df_ladder.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 4
     L.dsrg_df_ladder.restype = ctypes.c_int
     L.dsrg_df_ladder_noalloc.argtypes = [ctypes.c_int] * 5 + [ctypes.c_void_p] * 4
@@ -211,19 +215,36 @@ def dsrg_profile(h, enable: bool) -> None:
 
 
 def dsrg_profile_stats(h) -> dict:
-    """{kernel name: dict(launches, ms, flops, bytes)} accumulated since dsrg_profile."""
+    """{kernel name: dict(launches, ms, flops, exec_flops, bytes)} accumulated since dsrg_profile."""
     L = load_library()
     out = {}
     k = 0
     while True:
         name = ctypes.c_char_p()
         n = ctypes.c_longlong()
-        ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        ms, fl, xf, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         rc = L.dsrg_profile_stats(h, k, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
-                                  ctypes.byref(by))
+                                  ctypes.byref(xf), ctypes.byref(by))
         if rc != 0:
             break
-        out[name.value.decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+        out[name.value.decode()] = dict(launches=n.value, ms=ms.value, flops=fl.value, exec_flops=xf.value,
+                                        bytes=by.value)
+        k += 1
+    return out
+
+
+def dsrg_profile_steps(h) -> dict:
+    """{step name: dict(launches, ms, flops)} accumulated since dsrg_profile, in order of first use."""
+    L = load_library()
+    out = {}
+    k = 0
+    while True:
+        name = ctypes.c_char_p()
+        n = ctypes.c_longlong()
+        ms, fl = ctypes.c_double(), ctypes.c_double()
+        if L.dsrg_profile_step(h, k, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl)) != 0:
+            break
+        out[name.value.decode() or "other"] = dict(launches=n.value, ms=ms.value, flops=fl.value)
         k += 1
     return out
 
@@ -308,6 +329,9 @@ class Dsrg:
 
     def profile_stats(self):
         return dsrg_profile_stats(self.h)
+
+    def profile_steps(self):
+        return dsrg_profile_steps(self.h)
 
     @property
     def launches(self):

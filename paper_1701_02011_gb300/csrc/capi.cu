@@ -370,7 +370,7 @@ int dsrg_profile(dsrg_handle* hd, int enable) {
 }
 
 int dsrg_profile_stats(const dsrg_handle* hd, int kernel, const char** name, long long* launches, double* ms,
-                       double* flops, double* bytes) {
+                       double* flops, double* exec_flops, double* bytes) {
   if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
   if (kernel < 0 || kernel >= dsrg::K_NKERNELS) return fail(DSRG_ERR_ARG, "kernel index out of range");
   const dsrg::Workspace& w = hd->h->ws;
@@ -378,7 +378,21 @@ int dsrg_profile_stats(const dsrg_handle* hd, int kernel, const char** name, lon
   if (launches) *launches = w.prof_launches[kernel];
   if (ms) *ms = w.prof_ms[kernel];
   if (flops) *flops = w.prof_flops[kernel];
+  if (exec_flops) *exec_flops = w.prof_xflops[kernel];
   if (bytes) *bytes = w.prof_bytes[kernel];
+  return DSRG_OK;
+}
+
+int dsrg_profile_step(const dsrg_handle* hd, int step, const char** name, long long* launches, double* ms,
+                      double* flops) {
+  if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
+  const dsrg::Workspace& w = hd->h->ws;
+  if (step < 0 || step >= (int)w.prof_steps.size()) return fail(DSRG_ERR_ARG, "step index out of range");
+  const auto& x = w.prof_steps[step];
+  if (name) *name = x.name.c_str();
+  if (launches) *launches = x.launches;
+  if (ms) *ms = x.ms;
+  if (flops) *flops = x.flops;
   return DSRG_OK;
 }
 

@@ -297,13 +297,18 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
   size_t nL = (size_t)p * p * hh * hh;
   double* L = h.ws.get(nL, capL);
   check_cuda(cudaMemsetAsync(L, 0, nL * sizeof(double), h.ws.stream), "memset");
+  // (pr|qs) in batches of rows within a budget (DSRG_LADDER_BUDGET_MB,
+  // default 1024 MB); the first-order alpha-beta amplitudes have
+  // t[r,s,i,j] = t[s,r,j,i], so the pair-symmetric form applies
+  double budget_mb = 1024.0;
+  if (const char* env = getenv("DSRG_LADDER_BUDGET_MB")) budget_mb = atof(env);
+  long long maxd = (long long)(budget_mb * 131072.0);
   const long long p3 = (long long)p * p * p;
-  long long bp = ladder_batch_rows(p, 1LL << 27);  // <= 1 GiB of (pr|qs) per batch
-  if (bp < 1) bp = 1;
+  if (maxd < p3) maxd = p3;  // one row p with every q >= p0 (the first batch)
   size_t capG;
-  double* G = h.ws.get((size_t)(bp * p3), capG);
+  double* G = h.ws.get((size_t)maxd, capG);
   const long long tst[4] = {tv.st[0], tv.st[1], tv.st[2], tv.st[3]};
-  ladder_core(h.B, h.n, h.naux, h.nc, p, hh, t, tst, L, G, bp, h.ws.stream, &h.ws);
+  ladder_core_sym(h.B, h.n, h.naux, h.nc, p, hh, t, tst, L, G, maxd, h.ws.stream, &h.ws);
   h.ws.put(G, capG);
   // scatter into the spin blocks of C2 [2p][2p][2h][2h]
   const View& c = C2.v;

@@ -67,14 +67,15 @@ const char* kernel_name(int id) {
 void Workspace::prof_reset() {
   for (int i = 0; i < K_NKERNELS; ++i) {
     prof_launches[i] = 0;
-    prof_ms[i] = prof_flops[i] = prof_bytes[i] = 0.0;
+    prof_ms[i] = prof_flops[i] = prof_bytes[i] = prof_xflops[i] = 0.0;
   }
+  prof_steps.clear();
 }
 
-int Workspace::begin(int id, double flops, double bytes) {
+int Workspace::begin(int id, double flops, double bytes, double xflops) {
   launches++;
   if (!profiling) return -1;
-  Rec r{id, nullptr, nullptr, flops, bytes, 0, 0, 0, tag};
+  Rec r{id, nullptr, nullptr, flops, xflops < 0.0 ? flops : xflops, bytes, 0, 0, 0, tag};
   for (cudaEvent_t* e : {&r.a, &r.b}) {
     if (!ev_pool.empty()) {
       *e = ev_pool.back();
@@ -106,9 +107,10 @@ void Workspace::prof_collect() {
     std::sort(order.begin(), order.end(), [](auto& x, auto& y) { return x.first > y.first; });
     for (int i = 0; i < (int)order.size() && i < atoi(top); ++i) {
       const Rec& r = recs[order[i].second];
-      fprintf(stderr, "[dsrg] %-10s %9.3f ms  M=%lld N=%lld K=%lld  %.3f TFLOP/s %.0f GB/s  %s\n", kernel_name(r.id),
-              order[i].first, r.m, r.n, r.k, r.flops / (order[i].first * 1e-3) / 1e12,
-              r.bytes / (order[i].first * 1e-3) / 1e9, r.tag ? r.tag : "");
+      fprintf(stderr, "[dsrg] %-10s %9.3f ms  M=%lld N=%lld K=%lld  %.3f TFLOP/s (executed %.3f) %.0f GB/s  %s\n",
+              kernel_name(r.id), order[i].first, r.m, r.n, r.k, r.flops / (order[i].first * 1e-3) / 1e12,
+              r.xflops / (order[i].first * 1e-3) / 1e12, r.bytes / (order[i].first * 1e-3) / 1e9,
+              r.tag ? r.tag : "");
     }
   }
   for (auto& r : recs) {
@@ -117,7 +119,17 @@ void Workspace::prof_collect() {
     prof_launches[r.id]++;
     prof_ms[r.id] += ms;
     prof_flops[r.id] += r.flops;
+    prof_xflops[r.id] += r.xflops;
     prof_bytes[r.id] += r.bytes;
+    const char* t = r.tag ? r.tag : "";
+    auto it = std::find_if(prof_steps.begin(), prof_steps.end(), [&](const StepStat& x) { return x.name == t; });
+    if (it == prof_steps.end()) {
+      prof_steps.push_back(StepStat{t});
+      it = prof_steps.end() - 1;
+    }
+    it->launches++;
+    it->ms += ms;
+    it->flops += r.flops;
     ev_pool.push_back(r.a);
     ev_pool.push_back(r.b);
   }

@@ -107,14 +107,21 @@ class Workspace {
   // opt-in per-launch timing
   bool profiling = false;
   const char* tag = "";  // step of the energy being issued (profile output only)
-  struct Rec { int id; cudaEvent_t a, b; double flops, bytes; long long m, n, k; const char* tag; };
+  struct Rec { int id; cudaEvent_t a, b; double flops, xflops, bytes; long long m, n, k; const char* tag; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> ev_pool;
   long long prof_launches[K_NKERNELS] = {0};
   double prof_ms[K_NKERNELS] = {0}, prof_flops[K_NKERNELS] = {0}, prof_bytes[K_NKERNELS] = {0};
+  double prof_xflops[K_NKERNELS] = {0};
+  // per step of the energy (the tag in force at the launch), in order of first use
+  struct StepStat { std::string name; long long launches = 0; double ms = 0, flops = 0; };
+  std::vector<StepStat> prof_steps;
   void prof_reset();
-  // brackets one launch; call begin() before and end() after it
-  int begin(int id, double flops, double bytes);
+  // brackets one launch; call begin() before and end() after it.  flops: the
+  // FP64 flops of the contraction it computes (2 M N K); xflops: the flops
+  // the hardware executes (split products: digit pairs and tile padding;
+  // < 0: same as flops); bytes: algorithmic bytes of element-wise kernels
+  int begin(int id, double flops, double bytes, double xflops = -1.0);
   void end(int rec);
   void prof_collect();  // after the stream is synchronised
 

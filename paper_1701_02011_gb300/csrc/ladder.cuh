@@ -14,6 +14,12 @@ namespace dsrg {
 // Launches go through `ws` (counted, optionally timed) when it is non-null.
 void ladder_core(const double* B, long long n, int naux, int p0, int np, int nh, const double* t,
                  const long long* tst, double* L, double* G, long long bp, cudaStream_t st, Workspace* ws);
+// The same sum for a t with t[r,s,i,j] = t[s,r,j,i] (L must be zero on
+// entry), using (pr|qs) = (qs|pr): about half the work; G holds at most
+// max_doubles doubles.
+void ladder_core_sym(const double* B, long long n, int naux, int p0, int np, int nh, const double* t,
+                     const long long* tst, double* L, double* G, long long max_doubles, cudaStream_t st,
+                     Workspace* ws);
 // Largest batch of p rows whose (pr|qs) fits in max_doubles (0 if none).
 long long ladder_batch_rows(int np, long long max_doubles);
 int ladder_check_args(int n, int naux, int p0, int np, int nh, const void* B, const void* t, const void* L,

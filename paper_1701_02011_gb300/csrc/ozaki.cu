@@ -949,9 +949,13 @@ void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoic
   a.ktper = ktper;
   a.part = part;
   a.rowfast = (a.nM > 0 && a.nN > 0 && a.cM[a.nM - 1] < a.cN[a.nN - 1]) || (a.nN == 0 && a.nM > 0) ? 1 : 0;
-  // executed tensor-core flops: digit pairs with t + u <= S + 1, padded tiles
+  // timed as the tensor-core kernel whatever the contraction (kind is the
+  // step it belongs to); flops: the FP64 product it computes, executed:
+  // digit pairs with t + u <= S + 1 over the padded tiles
+  (void)kind;
   const double pairs = (double)S * (S + 1) / 2.0;
-  r = ws.begin(kind, 2.0 * pairs * (double)MT * OZ_BM * (double)NT * BN * (double)KT * OZ_BK, 0.0);
+  r = ws.begin(K_OZAKI_MMA, 2.0 * (double)M * (double)N * (double)g0.K, 0.0,
+               2.0 * pairs * (double)MT * OZ_BM * (double)NT * BN * (double)KT * OZ_BK);
   if (r >= 0) {
     ws.recs[r].m = M;
     ws.recs[r].n = N;

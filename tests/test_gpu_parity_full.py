@@ -1,0 +1,91 @@
+"""GPU parity at full workload sizes.
+
+* CAS(6,6), 10 core, 100 virtual, 400 auxiliary (the plain-FP64 workload):
+  the FP64 path against the CPU oracle's energies (oracle.dsrg_df, written to
+  tests/golden/ by tests/golden/make_golden.py, which calls only the oracle)
+  within 1e-9 Eh per component, and the split-precision path within 1e-6 Eh.
+  The test regenerates the seeded input and checks it against the recorded
+  fingerprints first, so both sides see the same problem.
+* CAS(8,8), 30 core, 300 virtual, 1200 auxiliary (the mixed-precision
+  workload, too large for the oracle): the split path with 8 digit slices
+  against the FP64 path, every component within 1e-6 Eh, in the launch
+  configuration the benchmark times.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+COMPONENTS = ("e2", "e3a", "e3b", "e3")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1701_02011_gb300 import build
+    build.build()
+    import paper_1701_02011_gb300 as g
+    g.load_library()
+    return g
+
+
+def _check_fingerprints(inst, rec):
+    for k, f in rec["inputs"].items():
+        a = np.ascontiguousarray(inst[k], dtype=np.float64).ravel()
+        assert a.size == f["size"], k
+        alt = np.where(np.arange(a.size) % 2 == 0, 1.0, -1.0)
+        for name, v in (("sum", np.sum(a)), ("sumsq", np.dot(a, a)), ("altsum", np.dot(a, alt))):
+            assert abs(v - f[name]) <= 1e-10 * max(1.0, abs(f[name]), float(np.dot(a, a)) ** 0.5), (k, name)
+
+
+def _device(inst):
+    import torch
+    return {k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
+            for k, v in inst.items()}
+
+
+def test_cas66_fp64_and_split_against_oracle(lib):
+    rec = json.load(open(os.path.join(HERE, "golden", "oracle_cas66_c10_v100_q400.json")))
+    inst = synth.config_instance(rec["workload"])
+    _check_fingerprints(inst, rec)
+    ref = rec["energies_Eh"]
+    dev = _device(inst)
+    h = lib.Dsrg(dev)
+    try:
+        e64 = h.pt3()
+    finally:
+        h.close()
+    for k in COMPONENTS:
+        assert abs(e64[k] - ref[k]) < 1e-9, (k, e64[k], ref[k])
+    h = lib.Dsrg(dev, precision=lib.DSRG_PREC_SPLIT, slices=6, tune=True)
+    try:
+        es = h.pt3()
+    finally:
+        h.close()
+    for k in COMPONENTS:
+        assert abs(es[k] - ref[k]) < 1e-6, (k, es[k], ref[k])
+
+
+def test_cas88_split_against_fp64(lib):
+    inst = synth.config_instance("cas88_c30_v300_q1200")
+    dev = _device(inst)
+    h = lib.Dsrg(dev, precision=lib.DSRG_PREC_SPLIT, slices=8, tune=True)
+    try:
+        es = h.pt3()
+    finally:
+        h.close()
+    h = lib.Dsrg(dev)
+    try:
+        e64 = h.pt3()
+    finally:
+        h.close()
+    for k in COMPONENTS:
+        assert abs(es[k] - e64[k]) < 1e-6, (k, es[k], e64[k])
