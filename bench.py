@@ -208,6 +208,38 @@ class OracleSample:
                 f"ladder alone, an upper bound on the oracle's rate for whole energies")
 
 
+def _cpu_baseline_main(workload, seconds, queue):
+    import synth
+    inst = synth.config_instance(workload)
+    smp = OracleSample(inst)
+    secs, rows = 0.0, 0
+    while (secs < seconds or rows == 0) and rows < smp.s.nrows:
+        dt, nr = smp.step(1)
+        secs += dt
+        rows += nr
+    queue.put({"value": smp.rate(secs, rows), "unit": "energies/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": smp.text(rows, secs)})
+
+
+def cpu_baseline_child(workload, seconds):
+    """The oracle sample in a spawned child process (this process holds a
+    CUDA context), so that a host-memory failure of the sample cannot take
+    the GPU measurement with it."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_cpu_baseline_main, args=(workload, seconds, q))
+    p.start()
+    out = None
+    try:
+        out = q.get(timeout=1800)
+    except Exception as e:  # noqa: BLE001 - the child died or timed out
+        out = {"value": None, "unit": "energies/s", "kind": "oracle", "cores": cpu_threads(),
+               "sample": f"oracle sample failed: {type(e).__name__} (exit code {p.exitcode})"}
+    p.join(timeout=60)
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -430,14 +462,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h, "steps": len(e2e_ms)},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        smp = OracleSample(inst)
-        secs, rows = 0.0, 0
-        while secs < args.cpu_seconds and rows < smp.s.nrows:
-            dt, nr = smp.step(1)
-            secs += dt
-            rows += nr
-        line["cpu_baseline"] = {"value": smp.rate(secs, rows), "unit": "energies/s", "cores": cpu_threads(),
-                                "kind": "oracle", "sample": smp.text(rows, secs)}
+        line["cpu_baseline"] = cpu_baseline_child(wl, args.cpu_seconds)
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:

@@ -94,7 +94,11 @@ typedef struct {
                      widths and k splits (on the caller's operands with
                      alpha = 0, so nothing changes) and keeps the fastest;
                      0 = fixed rules.  Results differ from the fixed rules
-                     only in summation order.  No counterpart in the paper. */
+                     only in summation order.  With the environment
+                     variable DSRG_TUNE_CACHE naming a file, decisions are
+                     read from it (keyed by product shape, slices and GPU
+                     model) and new ones appended, so later processes skip
+                     the timing.  No counterpart in the paper.           */
   long long wait_limit; /* budget, in SM clock cycles, of every bounded wait
                      inside the split-precision kernel (on copies and
                      tensor-core products it issued itself); 0 selects 2^32

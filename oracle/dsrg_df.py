@@ -404,7 +404,10 @@ class BlockProblem:
     # t^{ij}_{ab} = o^{ij}_{ab} R(D^{ij}_{ab}), t^i_a = [o^i_a + sum_ux D^u_x t^{iu}_{ax} gamma^x_u] R(D^i_a)
     def amplitudes(self, o1, o2):
         s = self.s
-        T2 = np.where(self.mask2, o2 * regulariser(s, self.D2), 0.0)
+        T2 = np.empty(self.D2.shape)
+        for lo in range(0, T2.shape[0], 8):   # element-wise; in slabs to bound temporaries
+            sl = slice(lo, lo + 8)
+            T2[sl] = np.where(self.mask2[sl], o2[sl] * regulariser(s, self.D2[sl]), 0.0)
         src = self.gamma_source(T2)
         T1 = np.where(self.mask1, (o1 + src) * regulariser(s, self.D1), 0.0)
         return T1, T2, src

@@ -373,6 +373,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   const Iv& A = h.A;
   const bool exc = (C2.v.iv[0].lo == P.lo && C2.v.iv[0].hi == P.hi);
   // [X1, T1] one-body: X1 T1 - T1 X1
+  ws.tag = "c-x1";
   contract(ws, 1.0, X1.v, "pr", T1.v, "rq", C1, "pq");
   contract(ws, -1.0, T1.v, "pr", X1.v, "rq", C1, "pq");
   // [X1, T2] one-body: (gamma X1 eta - eta X1 gamma)[i,a] T2[a,b,i,j]
@@ -402,6 +403,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     }
   }
   // [X2, T1] one-body: X2[p,q,s,r] (gamma T1^T eta)[q,r]
+  ws.tag = "c-x2t1";
   {
     Tensor tmp = mk(h, {H, P});
     contract(ws, 1.0, g.v, "qi", T1.v, "ai", tmp, "qa");
@@ -415,6 +417,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   contract_x2(ws, 1.0, X2, "qirs", T1.v, "pi", C2, "pqrs");
   contract_x2(ws, -1.0, X2, "pirs", T1.v, "qi", C2, "pqrs");
   // [X2, T2] one-body with three single contractions
+  ws.tag = "c-x2t2-1body";
   // dressed copies of T2, one chain at a time (each dressed in place after
   // its first copy), so that at most one is alive: [P,P,H,H] tensors set
   // the memory peak of the large instances
@@ -439,6 +442,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     contract_x2(ws, -0.5, X2, "pqrs", D4.v, "rbpq", C1, "bs");
   }
   // [X2, T2] one-body with a two-body cumulant
+  ws.tag = "c-cumulant";
   if (h.na > 0) {
     {
       Tensor Y = mk(h, {P, A});
@@ -484,6 +488,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     }
   }
   // [X2, T2] two-body: particle ladder 1/2 X2 T2 - X2[p,q,r,b] (gamma T2)[r,b,i,j]
+  ws.tag = "c-x2t2-2body";
   if (exc) {
     // the V part of the all-particle block is never stored: DF ladder
     if (X2.V && X2.cv != 0.0) {

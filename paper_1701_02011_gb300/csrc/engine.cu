@@ -19,6 +19,75 @@ void check_cuda(cudaError_t e, const char* what) {
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+namespace {
+std::string gpu_key() {
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaDeviceProp p{};
+  check_cuda(cudaGetDeviceProperties(&p, dev), "cudaGetDeviceProperties");
+  std::string name = p.name;
+  for (char& c : name)
+    if (c == ' ' || c == '\t') c = '_';
+  return name + "/sm" + std::to_string(p.multiProcessorCount) + "/cc" + std::to_string(p.major) +
+         std::to_string(p.minor);
+}
+
+std::mutex g_tc_mu;
+bool g_tc_loaded = false;
+std::map<std::string, std::vector<int>> g_tc;
+
+std::string tc_key(const char* kind, const std::string& gpu, long long M, long long N, long long K, int S) {
+  return std::string(kind) + " " + gpu + " " + std::to_string(M) + " " + std::to_string(N) + " " +
+         std::to_string(K) + " " + std::to_string(S);
+}
+
+// file lines: kind gpu M N K slices nvals v0 v1 ...
+void tc_load(const char* path) {
+  g_tc_loaded = true;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char kind[64], gpu[256];
+  long long M, N, K;
+  int S, nv;
+  while (fscanf(f, "%63s %255s %lld %lld %lld %d %d", kind, gpu, &M, &N, &K, &S, &nv) == 7) {
+    if (nv < 0 || nv > 8) break;
+    std::vector<int> v((size_t)nv);
+    bool ok = true;
+    for (int i = 0; i < nv && ok; ++i) ok = fscanf(f, "%d", &v[(size_t)i]) == 1;
+    if (!ok) break;
+    g_tc[tc_key(kind, gpu, M, N, K, S)] = v;
+  }
+  fclose(f);
+}
+}  // namespace
+
+bool tune_cache_lookup(const char* kind, long long M, long long N, long long K, int slices, int nvals, int* vals) {
+  const char* path = getenv("DSRG_TUNE_CACHE");
+  if (!path || !*path) return false;
+  const std::string key = tc_key(kind, gpu_key(), M, N, K, slices);
+  std::lock_guard<std::mutex> lock(g_tc_mu);
+  if (!g_tc_loaded) tc_load(path);
+  auto it = g_tc.find(key);
+  if (it == g_tc.end() || (int)it->second.size() != nvals) return false;
+  for (int i = 0; i < nvals; ++i) vals[i] = it->second[(size_t)i];
+  return true;
+}
+
+void tune_cache_store(const char* kind, long long M, long long N, long long K, int slices, int nvals,
+                      const int* vals) {
+  const char* path = getenv("DSRG_TUNE_CACHE");
+  if (!path || !*path) return;
+  const std::string gpu = gpu_key();
+  std::lock_guard<std::mutex> lock(g_tc_mu);
+  g_tc[tc_key(kind, gpu, M, N, K, slices)] = std::vector<int>(vals, vals + nvals);
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  std::string line = tc_key(kind, gpu, M, N, K, slices) + " " + std::to_string(nvals);
+  for (int i = 0; i < nvals; ++i) line += " " + std::to_string(vals[i]);
+  fprintf(f, "%s\n", line.c_str());
+  fclose(f);
+}
+
 View View::sub(const Iv* want) const {
   View o = *this;
   for (int k = 0; k < rank; ++k) {
@@ -157,6 +226,12 @@ bool split_faster(Workspace& ws, const GemmArgs& g) {
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
   }
+  int stored = 0;
+  if (tune_cache_lookup("route", g.M, g.N, g.K, ws.slices, 1, &stored)) {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = stored != 0;
+    return stored != 0;
+  }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   check_cuda(cudaStreamIsCapturing(ws.stream, &cs), "cudaStreamIsCapturing");
   if (cs != cudaStreamCaptureStatusNone) return false;
@@ -184,6 +259,8 @@ bool split_faster(Workspace& ws, const GemmArgs& g) {
   ws.profiling = prof;
   ws.launches = launches;
   const bool split = ms[1] < ms[0];
+  const int v = split ? 1 : 0;
+  tune_cache_store("route", g.M, g.N, g.K, ws.slices, 1, &v);
   std::lock_guard<std::mutex> lock(mu);
   cache[key] = split;
   return split;

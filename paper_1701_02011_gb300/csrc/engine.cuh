@@ -201,6 +201,15 @@ View w_place(const Tensor& W, int herm);
 
 void check_cuda(cudaError_t e, const char* what);
 
+// Persistent record of tuning decisions (file named by DSRG_TUNE_CACHE; no
+// file: decisions live for the process only).  A decision is a few integers
+// stored under (kind, GPU, M, N, K, slices); the GPU is identified by its
+// name, SM count and compute capability.  lookup fills `vals` and returns
+// true when the file holds the key; store appends a line.
+bool tune_cache_lookup(const char* kind, long long M, long long N, long long K, int slices, int nvals, int* vals);
+void tune_cache_store(const char* kind, long long M, long long N, long long K, int slices, int nvals,
+                      const int* vals);
+
 // launches through the workspace (counted, optionally timed)
 void run_gemm(Workspace& ws, const GemmArgs& g, int kind = K_GEMM);
 void run_axpy(Workspace& ws, const NdArgs& g, double alpha, const double* A, double* C);

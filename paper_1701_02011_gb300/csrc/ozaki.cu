@@ -14,9 +14,12 @@
 namespace dsrg {
 namespace {
 
-constexpr int OZ_BM = 128, OZ_BK = 64;
+// k per stage (a 64-byte row of bf16 digits), and stages per exact window:
+// a level sum over one window has at most 8 pairs x 128 products of
+// |d| <= 127, 8 x 128 x 127^2 < 2^24, so it is exact in FP32
+constexpr int OZ_BM = 128, OZ_BK = 32, OZ_WIN = 4;
 constexpr int OZ_THREADS = 256;  // 8 warps: lane quadrant (warp % 4) x column half (warp / 4)
-constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // A tile: 8192 bf16 = 16 KiB
+constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // A stage tile of one slice: 4096 bf16 = 8 KiB
 constexpr int OZ_TILE_BYTES = OZ_TILE_ELEMS * 2;
 // exponents are stored as 2048 + frexp exponent of the row / column maximum (0: all zero)
 constexpr unsigned OZ_EBIAS = 2048;
@@ -29,15 +32,16 @@ __device__ int g_oz_status;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzled
-// layout (rows of 64 bf16, 8-row groups 1024 bytes apart).
+// Shared-memory matrix descriptor: K-major operand in the 64-byte swizzled
+// layout (rows of 32 bf16, 8-row groups 512 bytes apart; the 16-byte chunk c
+// of row r sits at chunk c ^ ((r >> 1) & 3)).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
   d |= (uint64_t)1 << 16;                    // leading byte offset (unused when swizzled)
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: 8 rows x 64 B
   d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  d |= (uint64_t)4 << 61;                    // 64-byte swizzle
   return d;
 }
 
@@ -212,23 +216,26 @@ __device__ __forceinline__ double f32_to_f64_scaled(uint32_t u, int k) {
 }
 
 // One CTA: a 128 x BN tile of C with 8 warps; warp w reads TMEM lanes
-// 32 (w % 4) .. (tile rows) and column half w / 4.  Per k tile, thread 0
-// issues the MMAs of level c + 1 into one TMEM accumulator while all warps
-// fold level c out of the other one; the next k tile's bulk copies start as
-// soon as the last level's MMAs have completed.
+// 32 (w % 4) .. and column half w / 4.  The k range is walked in stages of
+// 32; two shared-memory buffers alternate, so the bulk copies of stage k + 1
+// run while the tensor cores work on stage k.  Every level c = t + u has its
+// own TMEM accumulator (S levels x BN columns); thread 0 issues all digit
+// pairs of a stage into them, and after every OZ_WIN stages (an exact window)
+// all warps fold the level sums, scaled by 2^(-7c), into float-float (hi, lo)
+// running sums held in registers.
 template <int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
-  constexpr uint32_t TMEM_COLS = BN == 128 ? 512 : BN == 64 ? 256 : 128;
+  constexpr uint32_t TMEM_COLS = 512;  // S <= 8 level accumulators of BN <= 64 columns
   constexpr int B_TILE_BYTES = BN * OZ_BK * 2;
   constexpr uint32_t IDESC = oz_idesc<BN>();
   // columns per warp in the fold and epilogue: two column halves for BN >= 64;
   // for BN = 32 the second half of the warps sits out
   constexpr int HALF = BN >= 64 ? BN / 2 : BN;
+  constexpr int NCH = HALF / 32;
+  static_assert(8 * BN <= (int)TMEM_COLS, "TMEM columns");
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + (size_t)a.S * OZ_TILE_BYTES;
-  __shared__ uint64_t bar_mma[2], bar_load;
+  __shared__ uint64_t bar_load[2], bar_mma[2], bar_win;
   __shared__ uint32_t tmem_base;
   __shared__ long long colC[BN], rowC[OZ_BM];
   __shared__ int colE[BN];
@@ -238,6 +245,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
   const int kt0 = a.splits > 1 ? z * a.ktper : 0;
   const int kt1 = a.splits > 1 ? (kt0 + a.ktper < a.KT ? kt0 + a.ktper : a.KT) : a.KT;
+  const int S = a.S;
+  const size_t stage_bytes = (size_t)S * (OZ_TILE_BYTES + B_TILE_BYTES);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -246,9 +255,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bar_mma[0], 1);
-    mbar_init(&bar_mma[1], 1);
-    mbar_init(&bar_load, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_load[i], 1);
+      mbar_init(&bar_mma[i], 1);
+    }
+    mbar_init(&bar_win, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int t = tid; t < BN; t += OZ_THREADS) {
@@ -266,150 +277,155 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   const uint32_t tm = tmem_base;
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   const uint32_t col0 = (uint32_t)(half * HALF);
-  const int nchunk = (BN >= 64 || half == 0) ? HALF / 32 : 0;  // 32-column chunks of this warp
+  const bool active = BN >= 64 || half == 0;
 
-  // TMEM columns: level accumulators [0, BN) and [BN, 2BN) (levels alternate),
-  // running float-float sum hi [2BN, 3BN) and lo [3BN, 4BN)
-  constexpr uint32_t HI = 2 * BN, LO = 3 * BN;
-  static_assert(4 * BN <= (int)TMEM_COLS, "TMEM columns");
-  {
-    uint32_t zr[32];
+  // running float-float sums of this thread's row and NCH x 32 columns
+  uint32_t rhi[NCH][32], rlo[NCH][32];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) zr[q] = 0u;
+  for (int j = 0; j < NCH; ++j)
 #pragma unroll
-    for (int j = 0; j < nchunk; ++j) {
-      tmem_st32(tm + lane_off + HI + col0 + 32 * j, zr);
-      tmem_st32(tm + lane_off + LO + col0 + 32 * j, zr);
-    }
-    tmem_wait_st();
-  }
-  const int S = a.S, L = S + 1;  // levels c = 2 .. S + 1
-  // thread 0: bulk copies of the S digit tiles of A and of B for k tile kt
-  auto issue_loads = [&](int kt) {
-    mbar_expect_tx(&bar_load, (uint32_t)(S * (OZ_TILE_BYTES + B_TILE_BYTES)));
+    for (int q = 0; q < 32; ++q) rhi[j][q] = rlo[j][q] = 0u;
+
+  // thread 0 only: copies of stage k (relative to kt0) into buffer k & 1
+  auto issue_load = [&](int k) {
+    const int b = k & 1, kt = kt0 + k;
+    unsigned char* base = smem + (size_t)b * stage_bytes;
+    mbar_expect_tx(&bar_load[b], (uint32_t)(S * (OZ_TILE_BYTES + B_TILE_BYTES)));
     for (int s = 0; s < S; ++s) {
-      bulk_g2s(sA + (size_t)s * OZ_TILE_BYTES, a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS,
-               OZ_TILE_BYTES, &bar_load);
-      bulk_g2s(sB + (size_t)s * B_TILE_BYTES, a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * (BN * OZ_BK),
-               B_TILE_BYTES, &bar_load);
+      bulk_g2s(base + (size_t)s * OZ_TILE_BYTES, a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS,
+               OZ_TILE_BYTES, &bar_load[b]);
+      bulk_g2s(base + (size_t)S * OZ_TILE_BYTES + (size_t)s * B_TILE_BYTES,
+               a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * (BN * OZ_BK), B_TILE_BYTES, &bar_load[b]);
     }
   };
-  // thread 0: the MMAs of level c (pairs t + u = c) into accumulator c & 1
-  auto issue_level = [&](int c) {
-    const uint32_t d = tm + (uint32_t)((c & 1) * BN);
-    uint32_t accum = 0;
-    const int t0 = c - S > 1 ? c - S : 1, t1 = c - 1 < S ? c - 1 : S;
-    for (int t = t0; t <= t1; ++t) {
-      const int u = c - t;
-      const uint32_t aA = smem_u32(sA + (size_t)(t - 1) * OZ_TILE_BYTES);
-      const uint32_t aB = smem_u32(sB + (size_t)(u - 1) * B_TILE_BYTES);
+  // thread 0 only: every digit pair (t, u), t + u <= S + 1, of stage k into
+  // the accumulator of level t + u; the first stage of a window overwrites
+  // (the first pair met for every level is t = 1)
+  auto issue_mmas = [&](int k, bool fresh) {
+    const int b = k & 1;
+    unsigned char* base = smem + (size_t)b * stage_bytes;
+    for (int t = 1; t <= S; ++t) {
+      const uint32_t aA = smem_u32(base + (size_t)(t - 1) * OZ_TILE_BYTES);
+      for (int u = 1; u <= S + 1 - t; ++u) {
+        const uint32_t d = tm + (uint32_t)((t + u - 2) * BN);
+        const uint32_t aB = smem_u32(base + (size_t)S * OZ_TILE_BYTES + (size_t)(u - 1) * B_TILE_BYTES);
 #pragma unroll
-      for (int ks = 0; ks < OZ_BK / 16; ++ks) {
-        mma_bf16(d, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), IDESC, accum);
-        accum = 1;
+        for (int ks = 0; ks < OZ_BK / 16; ++ks)
+          mma_bf16(d, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), IDESC, (fresh && t == 1 && ks == 0) ? 0u : 1u);
       }
     }
-    mma_commit(&bar_mma[c & 1]);
+    mma_commit(&bar_mma[b]);
   };
-  uint32_t ph_mma[2] = {0, 0}, ph_load = 0;
-  bool load_pending = false, mma_pending[2] = {false, false};  // meaningful in thread 0
+
+  uint32_t ph_load[2] = {0, 0}, ph_mma[2] = {0, 0}, ph_win = 0;
+  bool load_pending[2] = {false, false}, mma_pending[2] = {false, false}, win_pending = false;  // thread 0
   bool ok = true;
-  if (tid == 0 && kt0 < kt1) {
-    issue_loads(kt0);
-    load_pending = true;
+  const int ns = kt1 - kt0;
+  if (tid == 0 && ns > 0) {
+    issue_load(0);
+    load_pending[0] = true;
   }
-  for (int kt = kt0; kt < kt1 && ok; ++kt) {
-    ok = mbar_wait(&bar_load, ph_load, a.wait_cycles);
-    if (ok) ph_load ^= 1;  // a timed-out wait keeps its parity for the second wait
-    if (tid == 0 && ok) load_pending = false;
-    ok = __syncthreads_and(ok) != 0;
+  for (int k = 0; k < ns; ++k) {
+    const int b = k & 1;
+    const bool fresh = (k % OZ_WIN) == 0;
+    const bool wend = (k % OZ_WIN) == OZ_WIN - 1 || k == ns - 1;
+    if (tid == 0) {
+      if (ok) {
+        if (mbar_wait(&bar_load[b], ph_load[b], a.wait_cycles)) {
+          ph_load[b] ^= 1;
+          load_pending[b] = false;
+        } else {
+          ok = false;
+        }
+      }
+      if (ok) {
+        tc_fence_after();
+        issue_mmas(k, fresh);
+        mma_pending[b] = true;
+        // the other buffer is free once the MMAs of stage k - 1 completed
+        if (k + 1 < ns) {
+          const int b1 = (k + 1) & 1;
+          if (mma_pending[b1]) {
+            if (mbar_wait(&bar_mma[b1], ph_mma[b1], a.wait_cycles)) {
+              ph_mma[b1] ^= 1;
+              mma_pending[b1] = false;
+            } else {
+              ok = false;
+            }
+          }
+          if (ok) {
+            issue_load(k + 1);
+            load_pending[b1] = true;
+          }
+        }
+      }
+      if (wend) {  // completes once every MMA issued so far has completed
+        mma_commit(&bar_win);
+        win_pending = true;
+      }
+    }
+    if (!wend) continue;
+    const bool w = mbar_wait(&bar_win, ph_win, a.wait_cycles);
+    if (w) ph_win ^= 1;
+    if (tid == 0 && w) win_pending = false;
+    ok = __syncthreads_and(ok && w) != 0;
     tc_fence_after();
     if (!ok) break;
-    if (tid == 0) {
-      issue_level(2);
-      mma_pending[0] = true;
-    }
-    for (int c = 2; c <= L; ++c) {
-      // level c complete; start level c + 1 in the other accumulator (folded
-      // before the last barrier), or, after the last level, the next k tile
-      bool w = mbar_wait(&bar_mma[c & 1], ph_mma[c & 1], a.wait_cycles);
-      if (w) ph_mma[c & 1] ^= 1;
-      if (tid == 0 && w) mma_pending[c & 1] = false;
-      ok = __syncthreads_and(w) != 0;
-      tc_fence_after();
-      if (!ok) break;
-      if (tid == 0) {
-        if (c < L) {
-          issue_level(c + 1);
-          mma_pending[(c + 1) & 1] = true;
-        } else if (kt + 1 < kt1) {
-          issue_loads(kt + 1);
-          load_pending = true;
-        }
-      }
-      // fold level c: (hi, lo) += acc * 2^(-7c), two-sum in FP32
-      const float scale = exp2f(-7.0f * (float)c);
-      const uint64_t sc2 = f2_pack(__float_as_uint(scale), __float_as_uint(scale));
-      const uint32_t src = (uint32_t)((c & 1) * BN);
-#pragma unroll 1
-      for (int j = 0; j < nchunk; ++j) {
-        uint32_t acc[32], hi[32], lo[32];
-        const uint32_t cc = col0 + 32 * j;
-        tmem_ld32(tm + lane_off + src + cc, acc);
-        tmem_ld32(tm + lane_off + HI + cc, hi);
-        tmem_ld32(tm + lane_off + LO + cc, lo);
-        tmem_wait_ld();
-        // two columns per instruction (paired FP32, same IEEE rounding)
+    // fold the window: (hi, lo) += acc_c * 2^(-7c), two-sum in paired FP32
+    if (active) {
+      for (int c = 2; c <= S + 1; ++c) {
+        const float scale = exp2f(-7.0f * (float)c);
+        const uint64_t sc2 = f2_pack(__float_as_uint(scale), __float_as_uint(scale));
 #pragma unroll
-        for (int q = 0; q < 32; q += 2) {
-          const uint64_t x = f2_mul(f2_pack(acc[q], acc[q + 1]), sc2);
-          const uint64_t h = f2_pack(hi[q], hi[q + 1]);
-          const uint64_t s_ = f2_add(h, x);
-          const uint64_t bp = f2_sub(s_, h);
-          const uint64_t err = f2_add(f2_sub(h, f2_sub(s_, bp)), f2_sub(x, bp));
-          uint64_t l = f2_add(f2_pack(lo[q], lo[q + 1]), err);
-          const uint64_t s2 = f2_add(s_, l);
-          l = f2_sub(l, f2_sub(s2, s_));
-          f2_unpack(s2, hi[q], hi[q + 1]);
-          f2_unpack(l, lo[q], lo[q + 1]);
+        for (int j = 0; j < NCH; ++j) {
+          uint32_t acc[32];
+          tmem_ld32(tm + lane_off + (uint32_t)((c - 2) * BN) + col0 + 32 * j, acc);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 32; q += 2) {
+            const uint64_t x = f2_mul(f2_pack(acc[q], acc[q + 1]), sc2);
+            const uint64_t h = f2_pack(rhi[j][q], rhi[j][q + 1]);
+            const uint64_t s_ = f2_add(h, x);
+            const uint64_t bp = f2_sub(s_, h);
+            const uint64_t err = f2_add(f2_sub(h, f2_sub(s_, bp)), f2_sub(x, bp));
+            uint64_t l = f2_add(f2_pack(rlo[j][q], rlo[j][q + 1]), err);
+            const uint64_t s2 = f2_add(s_, l);
+            l = f2_sub(l, f2_sub(s2, s_));
+            f2_unpack(s2, rhi[j][q], rhi[j][q + 1]);
+            f2_unpack(l, rlo[j][q], rlo[j][q + 1]);
+          }
         }
-        tmem_st32(tm + lane_off + HI + cc, hi);
-        tmem_st32(tm + lane_off + LO + cc, lo);
       }
-      tmem_wait_st();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
     }
+    // the accumulators are read; the next window may overwrite them
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
   // after a timed-out wait: give the copies and MMAs still in flight a second
   // bounded wait (the fixed default budget) before the shared memory and TMEM
   // are released
   if (!ok && tid == 0) {
-    if (load_pending) mbar_wait(&bar_load, ph_load, OZ_WAIT_CYCLES);
     for (int i = 0; i < 2; ++i)
-      if (mma_pending[i]) mbar_wait(&bar_mma[i], ph_mma[i], OZ_WAIT_CYCLES);
+      if (load_pending[i]) mbar_wait(&bar_load[i], ph_load[i], OZ_WAIT_CYCLES);
+    if (win_pending) mbar_wait(&bar_win, ph_win, OZ_WAIT_CYCLES);
   }
   // epilogue: the scaled tile 2^(ea[m] + fb[n]) (hi + lo) goes to shared
-  // memory (the operand tiles are free once the last MMA has completed; rows
+  // memory (the stage buffers are free once the last MMA has completed; rows
   // padded by one double against bank conflicts), then consecutive threads
   // write consecutive columns of C (alpha times, accumulated) or of the
   // split-k partial part[z]
   constexpr int LDT = BN + 1;
   double* stile = reinterpret_cast<double*>(smem);
-  if (ok) {
+  if (ok && active) {
     const int em = a.ea[(long long)mt * OZ_BM + row] - (int)OZ_EBIAS;
-#pragma unroll 1
-    for (int j = 0; j < nchunk; ++j) {
-      uint32_t hi[32], lo[32];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
       const int cc = (int)col0 + 32 * j;
-      tmem_ld32(tm + lane_off + 2 * BN + cc, hi);
-      tmem_ld32(tm + lane_off + 3 * BN + cc, lo);
-      tmem_wait_ld();
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
         const int k = em + colE[cc + q];
-        stile[row * LDT + cc + q] = f32_to_f64_scaled(hi[q], k) + f32_to_f64_scaled(lo[q], k);
+        stile[row * LDT + cc + q] = f32_to_f64_scaled(rhi[j][q], k) + f32_to_f64_scaled(rlo[j][q], k);
       }
     }
   }
@@ -682,8 +698,8 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
       }
     }
     const unsigned tr = r / p.TR, rr = r - tr * p.TR;  // TR is 32, 64 or 128
-    const int tk = (int)(q >> 3), chunk = (int)(q & 7);
-    const long long within = (long long)rr * OZ_BK + ((chunk ^ (rr & 7)) << 3);
+    const int tk = (int)(q >> 2), chunk = (int)(q & 3);   // four 8-element chunks per 32-k row
+    const long long within = (long long)rr * OZ_BK + ((chunk ^ ((rr >> 1) & 3)) << 3);
 #pragma unroll
     for (int t = 1; t <= S; ++t) {
       uint32_t w[4];
@@ -727,7 +743,7 @@ inline int oz_grid(long long n) {
 }
 
 size_t oz_smem_bytes(int S, int BN) {
-  const size_t tiles = (size_t)S * OZ_TILE_BYTES + (size_t)S * BN * OZ_BK * 2;
+  const size_t tiles = 2 * ((size_t)S * OZ_TILE_BYTES + (size_t)S * BN * OZ_BK * 2);  // two stage buffers
   const size_t stage = (size_t)OZ_BM * (BN + 1) * sizeof(double);  // epilogue tile
   return (tiles > stage ? tiles : stage) + 1024;
 }
@@ -765,8 +781,7 @@ void oz_launch_bn(const OzArgs& a, int MT, int NT, cudaStream_t st) {
 
 void oz_launch_mma(const OzArgs& a, int MT, int NT, int BN, cudaStream_t st) {
   if (BN == 32) oz_launch_bn<32>(a, MT, NT, st);
-  else if (BN == 64) oz_launch_bn<64>(a, MT, NT, st);
-  else oz_launch_bn<128>(a, MT, NT, st);
+  else oz_launch_bn<64>(a, MT, NT, st);
 }
 }  // namespace
 
@@ -854,7 +869,7 @@ void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoic
       a.cN[d] = g0.cM[d];
     }
   }
-  int BN = ch.bn ? ch.bn : N <= 32 ? 32 : N <= 64 ? 64 : 128;
+  int BN = ch.bn ? ch.bn : N <= 32 ? 32 : 64;
   // shared memory per CTA is capped at 227 KiB (static arrays take up to 4 KiB)
   while (BN > 32 && oz_smem_bytes(S, BN) + 4096 > 227 * 1024) BN /= 2;
   const int MT = (int)((M + OZ_BM - 1) / OZ_BM), NT = (int)((N + BN - 1) / BN);
@@ -1002,6 +1017,17 @@ OzChoice choose(Workspace& ws, const GemmArgs& g0, int S, int kind) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second;
   }
+  int stored[2];
+  if (tune_cache_lookup("tile", g0.M, g0.N, g0.K, S, 2, stored)) {
+    OzChoice c;
+    c.bn = stored[0];
+    c.split_mode = stored[1];
+    if (c.bn == 32 || c.bn == 64) {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[key] = c;
+      return c;
+    }
+  }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   check_cuda(cudaStreamIsCapturing(ws.stream, &cs), "cudaStreamIsCapturing");
   if (cs != cudaStreamCaptureStatusNone) return def;
@@ -1010,7 +1036,7 @@ OzChoice choose(Workspace& ws, const GemmArgs& g0, int S, int kind) {
   const long long nshort = g0.M < g0.N ? g0.M : g0.N;
   const long long KT = (g0.K + OZ_BK - 1) / OZ_BK;
   std::vector<OzChoice> cands;
-  for (int bn : {32, 64, 128}) {
+  for (int bn : {32, 64}) {
     if (bn != 32 && bn / 2 >= nshort) continue;
     const long long big = g0.M > g0.N ? g0.M : g0.N;
     const long long ctas = ((big + OZ_BM - 1) / OZ_BM) * ((nshort + bn - 1) / bn);
@@ -1049,6 +1075,8 @@ OzChoice choose(Workspace& ws, const GemmArgs& g0, int S, int kind) {
   cudaEventDestroy(e1);
   ws.profiling = prof;
   ws.launches = launches;
+  const int v[2] = {best.bn, best.split_mode};
+  tune_cache_store("tile", g0.M, g0.N, g0.K, S, 2, v);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune[key] = best;
   return best;
