@@ -227,6 +227,32 @@ int dsrg_df_ladder_noalloc(int n, int naux, int p0, int np, int nh, const double
                            void *stream);
 
 /*
+ * Pivoted incomplete Cholesky factorisation of a two-electron supermatrix,
+ * giving the three-index factor of Eq. int_fact, (pq|rs) ~ sum_Q B^Q_pq B^Q_rs,
+ * as for the Cholesky integrals of the paper's larger applications (Sec. IV,
+ * thresholds 1e-6 and 1e-8 a.u.; algorithm of Beebe and Linderberg).
+ *   V       device [N][N], FP64, row-major, symmetric positive semidefinite
+ *           (for integrals N = n^2 and V[p n + q][r n + s] = (pq|rs)); read
+ *           by rows, never written
+ *   tau     threshold >= 0: the factorisation stops when the largest
+ *           remaining diagonal D[J] = V[J][J] - sum_Q B[Q][J]^2 is <= tau
+ *   max_vecs  capacity of B (stops there at the latest)
+ *   B       device [max_vecs][N] output: B[Q] = (V[J_Q] - sum_{Q'<Q} B[Q'] B[Q'][J_Q]) / sqrt(D[J_Q]),
+ *           J_Q the pivot of step Q (largest D, the smallest index on ties);
+ *           rows past *nvecs are left untouched
+ *   nvecs   host, receives the number of vectors formed
+ *   pivots  host [max_vecs] or NULL, receives J_0 .. J_{nvecs-1}
+ * Corrections are summed over Q' in increasing order with one rounding per
+ * product and per sum (no fused multiply-add), so results are reproducible
+ * operation by operation.  Scratch (N + max_vecs + a few thousand doubles)
+ * is allocated and released inside the call; synchronises `stream`.
+ * Errors: DSRG_ERR_ARG (sizes, tau < 0, NULL pointers), DSRG_ERR_OOM,
+ * DSRG_ERR_CUDA.
+ */
+int dsrg_cholesky(long long N, const double *V, double tau, int max_vecs, double *B, int *nvecs, long long *pivots,
+                  void *stream);
+
+/*
  * Split-precision FP64 matrix product on the tensor cores (no counterpart in
  * the paper: it is the contraction primitive of the mixed-precision path):
  *   C[m][n] += alpha * sum_k A[m][k] B[k][n]

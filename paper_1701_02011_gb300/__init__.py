@@ -48,7 +48,7 @@ class dsrg_energies(ctypes.Structure):
 EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_pt3_batch", "dsrg_free", "dsrg_last_error",
            "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
            "dsrg_profile_step",
-           "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc", "dsrg_split_gemm")
+           "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc", "dsrg_split_gemm", "dsrg_cholesky")
 
 _lib = None
 
@@ -99,6 +99,9 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
                                                             ctypes.c_void_p, ctypes.c_longlong,
                                                             ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
     L.dsrg_split_gemm.restype = ctypes.c_int
+    L.dsrg_cholesky.argtypes = [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong), ctypes.c_void_p]
+    L.dsrg_cholesky.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -301,6 +304,23 @@ def dsrg_split_gemm(A, B, C, alpha: float = 1.0, slices: int = 6, stream=None) -
                                           ctypes.c_void_p(B.data_ptr()), B.stride(0),
                                           ctypes.c_void_p(C.data_ptr()), C.stride(0), float(alpha), int(slices),
                                           ctypes.c_void_p(stream) if stream else None))
+
+
+def dsrg_cholesky(V, tau: float, max_vecs: int, stream=None):
+    """Pivoted incomplete Cholesky of the PSD CUDA float64 matrix V [N][N]:
+    returns (B [nvecs][N] CUDA tensor, pivots numpy int64 array)."""
+    import torch
+    N = V.shape[0]
+    if not (V.is_cuda and V.dtype == torch.float64 and V.is_contiguous() and tuple(V.shape) == (N, N)):
+        raise ValueError("expected a contiguous square CUDA float64 matrix")
+    B = torch.empty((max(max_vecs, 1), N), dtype=torch.float64, device=V.device)
+    n = ctypes.c_int(0)
+    piv = np.zeros(max(max_vecs, 1), dtype=np.int64)
+    _check(load_library().dsrg_cholesky(N, ctypes.c_void_p(V.data_ptr()), float(tau), int(max_vecs),
+                                        ctypes.c_void_p(B.data_ptr()), ctypes.byref(n),
+                                        piv.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                        ctypes.c_void_p(stream) if stream else None))
+    return B[: n.value], piv[: n.value]
 
 
 class Dsrg:

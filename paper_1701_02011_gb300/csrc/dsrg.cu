@@ -117,19 +117,28 @@ Tensor build_x1(Handle& h, double c_v, const Tensor* W1, double c_w) {
 }
 
 // V on the canonical classes HHHH, HHHP, HHPP, PHPH, PPPH (bits 0..4)
-// Classes larger than the budget (DSRG_V_CLASS_BUDGET_MB, default 8192 MB of
-// device memory per class) are not stored: the terms that read them build V
-// from B on their own intervals, a slab at a time within the same budget.
-// The [P,P,P,H] class is the one that grows past it (p^3 h: 53 GB at
-// p = 308, h = 38).
+// Classes larger than the budget are not stored: the terms that read them
+// build V from B on their own intervals, a slab at a time within the same
+// budget.  The budget is DSRG_V_CLASS_BUDGET_MB if set, else 30 % of the
+// device memory free at this point, at most 64 GB per class: the [P,P,P,H]
+// class (p^3 h; 53 GB at p = 308, h = 38) is then built once and read by
+// every term, instead of once per term; at p = 504, h = 44 (270 GB) it is
+// still built per use.
 void build_v(Handle& h, unsigned classes, Sym2& V) {
   V.cls.clear();
   V.make = nullptr;
   const Iv& H = h.H;
   const Iv& P = h.P;
-  double budget_mb = 8192.0;
-  if (const char* env = getenv("DSRG_V_CLASS_BUDGET_MB")) budget_mb = atof(env);
-  const double budget = budget_mb * 1048576.0;
+  double budget;
+  if (const char* env = getenv("DSRG_V_CLASS_BUDGET_MB")) {
+    budget = atof(env) * 1048576.0;
+  } else {
+    size_t free_b = 0, total_b = 0;
+    check_cuda(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    budget = 0.3 * (double)free_b;
+    if (budget > 64.0 * 1073741824.0) budget = 64.0 * 1073741824.0;
+    if (budget < 8.0 * 1073741824.0) budget = 8.0 * 1073741824.0;
+  }
   Iv cl[5][4] = {{H, H, H, H}, {H, H, H, P}, {H, H, P, P}, {P, H, P, H}, {P, P, P, H}};
   for (int c = 0; c < 5; ++c) {
     if (!((classes >> c) & 1)) continue;

@@ -46,10 +46,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, M = 128, N = BN.
-template <int BN>
-__host__ __device__ constexpr uint32_t oz_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+// K-major, M = 128, N columns (a multiple of 16, at most 256).
+__host__ __device__ constexpr uint32_t oz_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -227,7 +226,6 @@ template <int BN>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   constexpr uint32_t TMEM_COLS = 512;  // S <= 8 level accumulators of BN <= 64 columns
   constexpr int B_TILE_BYTES = BN * OZ_BK * 2;
-  constexpr uint32_t IDESC = oz_idesc<BN>();
   // columns per warp in the fold and epilogue: two column halves for BN >= 64;
   // for BN = 32 the second half of the warps sits out
   constexpr int HALF = BN >= 64 ? BN / 2 : BN;
@@ -299,19 +297,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     }
   };
   // thread 0 only: every digit pair (t, u), t + u <= S + 1, of stage k into
-  // the accumulator of level t + u; the first stage of a window overwrites
-  // (the first pair met for every level is t = 1)
+  // the accumulator of level t + u.  For a fixed A slice t the levels
+  // t + 1 .. S + 1 are adjacent in TMEM and the B slices 1 .. S + 1 - t are
+  // adjacent in shared memory, so one MMA of N = BN (S + 1 - t) columns (in
+  // pieces of at most 256) covers them all and reads A_t once.  The first
+  // stage of a window overwrites: the t = 1 MMAs cover every level.
   auto issue_mmas = [&](int k, bool fresh) {
     const int b = k & 1;
     unsigned char* base = smem + (size_t)b * stage_bytes;
+    constexpr int UMAX = 256 / BN;  // B slices per MMA
     for (int t = 1; t <= S; ++t) {
       const uint32_t aA = smem_u32(base + (size_t)(t - 1) * OZ_TILE_BYTES);
-      for (int u = 1; u <= S + 1 - t; ++u) {
-        const uint32_t d = tm + (uint32_t)((t + u - 2) * BN);
-        const uint32_t aB = smem_u32(base + (size_t)S * OZ_TILE_BYTES + (size_t)(u - 1) * B_TILE_BYTES);
+      for (int u0 = 1; u0 <= S + 1 - t; u0 += UMAX) {
+        const int nu = (S + 1 - t) - u0 + 1 < UMAX ? (S + 1 - t) - u0 + 1 : UMAX;
+        const uint32_t d = tm + (uint32_t)((t + u0 - 2) * BN);
+        const uint32_t aB = smem_u32(base + (size_t)S * OZ_TILE_BYTES + (size_t)(u0 - 1) * B_TILE_BYTES);
+        const uint32_t idesc = oz_idesc(nu * BN);
 #pragma unroll
         for (int ks = 0; ks < OZ_BK / 16; ++ks)
-          mma_bf16(d, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), IDESC, (fresh && t == 1 && ks == 0) ? 0u : 1u);
+          mma_bf16(d, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), idesc, (fresh && t == 1 && ks == 0) ? 0u : 1u);
       }
     }
     mma_commit(&bar_mma[b]);

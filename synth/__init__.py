@@ -255,10 +255,24 @@ def make_instance(nc: int, na: int, nel: int, nv: int, naux: int, s: float = 0.5
     return inst
 
 
+# large active spaces with synthetic references (make_synthetic_instance)
+SYNTHETIC_CONFIGS = {
+    "cas1616_c10_v100_q400": dict(nc=10, na=16, nv=100, naux=400, s=0.5, seed=SEED0 + 5),
+}
+
+
 def config_instance(name: str, **kw) -> dict:
+    if name in SYNTHETIC_CONFIGS:
+        c = dict(SYNTHETIC_CONFIGS[name])
+        c.update(kw)
+        return make_synthetic_instance(**c)
     c = dict(CONFIGS[name])
     c.update(kw)
     return make_instance(**c)
+
+
+def config_seed(name: str) -> int:
+    return (SYNTHETIC_CONFIGS.get(name) or CONFIGS[name])["seed"]
 
 
 def scan_sizes(j: int, nscan: int = 32) -> dict:
@@ -283,3 +297,71 @@ def scan_instance(j: int, nscan: int = 32) -> dict:
 
 def random_small(nc, na, nel, nv, naux, s=0.5, seed=1):
     return make_instance(nc, na, nel, nv, naux, s, seed=seed)
+
+
+# ----------------------------------------------------------------------------
+# synthetic references for large active spaces
+# ----------------------------------------------------------------------------
+
+def _symmetrised_block(rng, na, rank, groups, scale):
+    """Random block X[p1..pk, q1..qk] (each index over the na active orbitals
+    of one spin), Hermitian (X[p.., q..] = X[q.., p..]) and antisymmetric
+    under exchanges within each group of same-spin creator slots and the same
+    groups of annihilator slots (`groups`: tuples of slot positions 0..k-1)."""
+    from itertools import permutations as _perms
+    X = rng.standard_normal((na,) * (2 * rank))
+    X = X + np.transpose(X, list(range(rank, 2 * rank)) + list(range(rank)))
+    for grp in groups:
+        if len(grp) < 2:
+            continue
+        # antisymmetry: one group permutation on creators and one, independent, on annihilators
+        acc = np.zeros_like(X)
+        for pc in _perms(range(len(grp))):
+            for pa in _perms(range(len(grp))):
+                axes = list(range(2 * rank))
+                for i, j in zip(grp, pc):
+                    axes[i] = grp[j]
+                for i, j in zip(grp, pa):
+                    axes[rank + i] = rank + grp[j]
+                acc += _perm_sign(pc) * _perm_sign(pa) * np.transpose(X, axes)
+        X = acc
+    return X * scale
+
+
+def synthetic_reference(na: int, rng, l2_scale: float = 0.02, l3_scale: float = 0.002) -> dict:
+    """Spin blocks of a synthetic active-space reference for active spaces too
+    large for an exact CI (CAS(12,12) has 853776 Ms=0 determinants): gamma1
+    per spin a random symmetric matrix with eigenvalues in [0, 1] (natural
+    occupations); lambda2 and lambda3 blocks random with the symmetries of
+    density cumulants (Hermitian, antisymmetric under exchanges of same-spin
+    creators and of same-spin annihilators), small in magnitude.  They are
+    not the cumulants of any one state; the energy expressions take them as
+    given.  Blocks as spin_blocks returns them (alpha slots first)."""
+    out = {}
+    for k in ("g1a", "g1b"):
+        U, _ = np.linalg.qr(rng.standard_normal((na, na)))
+        occ = rng.uniform(0.0, 1.0, na)
+        out[k] = (U * occ) @ U.T
+    out["l2aa"] = _symmetrised_block(rng, na, 2, [(0, 1)], l2_scale)
+    out["l2ab"] = _symmetrised_block(rng, na, 2, [], l2_scale)
+    out["l2bb"] = _symmetrised_block(rng, na, 2, [(0, 1)], l2_scale)
+    out["l3aaa"] = _symmetrised_block(rng, na, 3, [(0, 1, 2)], l3_scale)
+    out["l3aab"] = _symmetrised_block(rng, na, 3, [(0, 1)], l3_scale)
+    out["l3abb"] = _symmetrised_block(rng, na, 3, [(1, 2)], l3_scale)
+    out["l3bbb"] = _symmetrised_block(rng, na, 3, [(0, 1, 2)], l3_scale)
+    return {k: np.ascontiguousarray(v) for k, v in out.items()}
+
+
+def make_synthetic_instance(nc: int, na: int, nv: int, naux: int, s: float = 0.5, seed: int = SEED0) -> dict:
+    """A problem with the orbital-energy and B^Q recipe of make_instance and a
+    synthetic reference (synthetic_reference) in place of the CI vector.
+    Draw order: core, active, virtual energies, gamma1 / lambda2 / lambda3,
+    then B row by row."""
+    rng = np.random.default_rng(seed)
+    eps = np.concatenate([rng.uniform(*EPS_CORE, nc), rng.uniform(*EPS_ACT, na), rng.uniform(*EPS_VIR, nv)])
+    ref = synthetic_reference(na, rng)
+    B = df_factor(rng, nc + na + nv, naux)
+    inst = dict(nc=nc, na=na, nv=nv, naux=naux, s=float(s), eps=eps, B=B)
+    for k in ("g1a", "g1b", "l2aa", "l2ab", "l2bb", "l3aaa", "l3aab", "l3abb", "l3bbb"):
+        inst[k] = ref[k]
+    return inst
