@@ -122,8 +122,19 @@ __global__ void __launch_bounds__(CH_T) k_chol_step(const double* __restrict__ V
   double bv = -INFINITY;
   long long bi = -1;
   for (long long i = blockIdx.x * (long long)CH_T + threadIdx.x; i < N; i += (long long)gridDim.x * CH_T) {
+    // the products of 16 vectors are loaded and formed ahead of their
+    // (sequential, increasing-q) additions, so many loads are in flight
     double acc = 0.0;
-    for (int q = 0; q < Q; ++q) acc = __dadd_rn(acc, __dmul_rn(B[(long long)q * N + i], bJ[(long long)q * N]));
+    int q = 0;
+    for (; q + 16 <= Q; q += 16) {
+      double pr[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        pr[u] = __dmul_rn(__ldg(B + (long long)(q + u) * N + i), __ldg(bJ + (long long)(q + u) * N));
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc = __dadd_rn(acc, pr[u]);
+    }
+    for (; q < Q; ++q) acc = __dadd_rn(acc, __dmul_rn(__ldg(B + (long long)q * N + i), __ldg(bJ + (long long)q * N)));
     const double L = __ddiv_rn(__dsub_rn(V[J * N + i], acc), sq);
     B[(long long)Q * N + i] = L;
     const double d = __dsub_rn(D[i], __dmul_rn(L, L));

@@ -116,15 +116,17 @@ Tensor build_x1(Handle& h, double c_v, const Tensor* W1, double c_w) {
   return X1;
 }
 
-// V on the canonical classes HHHH, HHHP, HHPP, PHPH, PPPH (bits 0..4)
+// V on the canonical classes HHHH, HHHP, HHPP, PHPH, PPPH (bits 0..4); with
+// on_demand, requests no stored class covers are built from B per use
 // Classes larger than the budget are not stored: the terms that read them
 // build V from B on their own intervals, a slab at a time within the same
-// budget.  The budget is DSRG_V_CLASS_BUDGET_MB if set, else 30 % of the
-// device memory free at this point, at most 64 GB per class: the [P,P,P,H]
-// class (p^3 h; 53 GB at p = 308, h = 38) is then built once and read by
-// every term, instead of once per term; at p = 504, h = 44 (270 GB) it is
-// still built per use.
-void build_v(Handle& h, unsigned classes, Sym2& V) {
+// budget.  The budget is DSRG_V_CLASS_BUDGET_MB if set, else 20 % of the
+// device's memory, at most 64 GB per class (the same for every energy of a
+// handle, whatever the buffer cache holds): the [P,P,P,H] class (p^3 h;
+// 53 GB at p = 308, h = 38) is then built once and read by every term,
+// instead of once per term; at p = 504, h = 44 (270 GB) it is still built
+// per use.
+void build_v(Handle& h, unsigned classes, Sym2& V, bool on_demand) {
   V.cls.clear();
   V.make = nullptr;
   const Iv& H = h.H;
@@ -133,9 +135,11 @@ void build_v(Handle& h, unsigned classes, Sym2& V) {
   if (const char* env = getenv("DSRG_V_CLASS_BUDGET_MB")) {
     budget = atof(env) * 1048576.0;
   } else {
-    size_t free_b = 0, total_b = 0;
-    check_cuda(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-    budget = 0.3 * (double)free_b;
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    cudaDeviceProp prop{};
+    check_cuda(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+    budget = 0.2 * (double)prop.totalGlobalMem;
     if (budget > 64.0 * 1073741824.0) budget = 64.0 * 1073741824.0;
     if (budget < 8.0 * 1073741824.0) budget = 8.0 * 1073741824.0;
   }
@@ -151,6 +155,11 @@ void build_v(Handle& h, unsigned classes, Sym2& V) {
       V.make = [hp](const Iv* ivs) { return vclass(*hp, ivs, 1.0); };
       V.max_elems = (long long)(budget / 8.0);
     }
+  }
+  if (on_demand && !V.make) {  // any other interval class: built from B per use
+    Handle* hp = &h;
+    V.make = [hp](const Iv* ivs) { return vclass(*hp, ivs, 1.0); };
+    V.max_elems = (long long)(budget / 8.0);
   }
 }
 
@@ -343,6 +352,165 @@ void df_ladder(Handle& h, const Tensor& T2, Tensor& C2, double coef) {
 }
 
 // ---------------------------------------------------------------------------
+// density-fitted forms of the two excitation-block terms that would read V
+// with three particle indices (p^3 h elements: 53 GB at p = 308, h = 38);
+// with (pq|rs) = sum_Q B^Q_pq B^Q_rs (Eq. int_fact) they contract small
+// three-index intermediates instead
+// ---------------------------------------------------------------------------
+namespace {
+// C[m0,m1][n0,n1] += alpha sum_k A[m0,m1][k..] B[k..][n0,n1] (K of one or two dims)
+struct Dims2 {
+  int e[2];
+  long long a[2], c[2];
+};
+void gemm22(Handle& h, double alpha, const double* A, const double* B, double* C, Dims2 m, Dims2 nn, int nk,
+            const int* ek, const long long* ak, const long long* bk) {
+  GemmArgs g{};
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.alpha = alpha;
+  g.nM = 2;
+  g.nN = 2;
+  g.nK = nk;
+  g.M = g.N = g.K = 1;
+  for (int i = 0; i < 2; ++i) {
+    g.eM[i] = m.e[i];
+    g.aM[i] = m.a[i];
+    g.cM[i] = m.c[i];
+    g.eN[i] = nn.e[i];
+    g.bN[i] = nn.a[i];
+    g.cN[i] = nn.c[i];
+    g.M *= m.e[i];
+    g.N *= nn.e[i];
+  }
+  for (int i = 0; i < nk; ++i) {
+    g.eK[i] = ek[i];
+    g.aK[i] = ak[i];
+    g.bK[i] = bk[i];
+    g.K *= ek[i];
+  }
+  g.nbatch = 1;
+  run_gemm(h.ws, g);
+}
+
+double* c2_block(Tensor& C2, int s0, int s1, int s2, int s3) {
+  const int bits = s0 | s1 << 1 | s2 << 2 | s3 << 3;
+  if (!((C2.v.stored >> bits) & 1)) throw std::runtime_error("df term: spin block not stored");
+  C2.v.mask |= 1ULL << bits;
+  return C2.v.p + C2.v.boff[bits];
+}
+}  // namespace
+
+// C2[p,q,r,s] += coef (sum_a V[p,q,a,s] T1[a,r] - sum_a V[p,q,a,r] T1[a,s]) on
+// the excitation block [P,P,H,H], V = <pq||rs>: with X^Q_pr = sum_a B^Q_pa T1[a,r]
+// (per spin), sum_a (pa|qs) T1[a,r] = sum_Q X^Q_pr B^Q_qs and
+// sum_a (ps|qa) T1[a,r] = sum_Q B^Q_ps X^Q_qr.  The Coulomb part of the first
+// term and the exchange part of the second land in the same spin blocks with
+// the same index pairing, as do the other two parts, so each pair is one
+// product over a stacked index k < 2Q: U^s = [X^s; B], W^s = [B; X^s] (the
+// B^Q_pr block over particles p and holes r copied next to X).
+static void df_x2t1(Handle& h, const Tensor& T1, Tensor& C2, double coef) {
+  const int p = h.na + h.nv, hh = h.nc + h.na, Q = h.naux;
+  if (p == 0 || hh == 0) return;
+  const long long n = h.n, n2 = n * n, P0 = h.nc, ph = (long long)p * hh, blk = (long long)Q * ph;
+  const View& t = T1.v;
+  bool has[2] = {false, false};
+  for (int sg = 0; sg < 2; ++sg) has[sg] = (t.mask >> (sg | sg << 1)) & 1;
+  if (!has[0] && !has[1]) return;
+  // U^s at U + 2s blk: [X^s, Bc]; W^s at W + 2s blk: [Bc, X^s]
+  size_t capU, capW;
+  double* U = h.ws.get((size_t)(4 * blk), capU);
+  double* W = h.ws.get((size_t)(4 * blk), capW);
+  check_cuda(cudaMemsetAsync(U, 0, (size_t)(4 * blk) * sizeof(double), h.ws.stream), "memset");
+  check_cuda(cudaMemsetAsync(W, 0, (size_t)(4 * blk) * sizeof(double), h.ws.stream), "memset");
+  {  // Bc[Q][p][r] = B[Q][P0+p][r] into U^s[1] and W^s[0]
+    NdArgs g{};
+    g.nd = 3;
+    g.e[0] = Q; g.sa[0] = n2; g.sb[0] = ph;
+    g.e[1] = p; g.sa[1] = n;  g.sb[1] = hh;
+    g.e[2] = hh; g.sa[2] = 1; g.sb[2] = 1;
+    g.total = blk;
+    for (int sg = 0; sg < 2; ++sg) {
+      launch_axpy(g, 1.0, h.B + P0 * n, U + (2 * sg + 1) * blk, h.ws.stream);
+      check_cuda(cudaMemcpyAsync(W + 2 * sg * blk, U + (2 * sg + 1) * blk, (size_t)blk * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, h.ws.stream), "cudaMemcpyAsync (df)");
+    }
+    h.ws.launches += 2;
+  }
+  for (int sg = 0; sg < 2; ++sg) {
+    if (!has[sg]) continue;
+    const int tb = sg | sg << 1;
+    // X^s[Q][p][r] = sum_a B[Q][P0+p][P0+a] T1^{ss}[a][r]
+    const int ek[1] = {p};
+    const long long ak[1] = {1}, bk[1] = {t.st[0]};
+    gemm22(h, 1.0, h.B + P0 * n + P0, t.p + t.boff[tb], U + 2 * sg * blk, Dims2{{Q, p}, {n2, n}, {ph, hh}},
+           Dims2{{1, hh}, {0, t.st[1]}, {0, 1}}, 1, ek, ak, bk);
+    check_cuda(cudaMemcpyAsync(W + (2 * sg + 1) * blk, U + 2 * sg * blk, (size_t)blk * sizeof(double),
+                               cudaMemcpyDeviceToDevice, h.ws.stream), "cudaMemcpyAsync (df)");
+  }
+  const View& c = C2.v;
+  const int ek[1] = {2 * Q};
+  const long long kk[1] = {ph};
+  for (int s1 = 0; s1 < 2; ++s1)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      // block (s1, s2, s1, s2) += sum_k U^s1[k][p][r] W^s2[k][q][s]
+      // (X^s1_pr B_qs + B_pr X^s2_qs); needs T1^{s1 s1} or T1^{s2 s2}
+      if (has[s1] || has[s2])
+        gemm22(h, coef, U + 2 * s1 * blk, W + 2 * s2 * blk, c2_block(C2, s1, s2, s1, s2),
+               Dims2{{p, hh}, {hh, 1}, {c.st[0], c.st[2]}}, Dims2{{p, hh}, {hh, 1}, {c.st[1], c.st[3]}}, 1, ek, kk,
+               kk);
+      // block (s2, s1, s1, s2) -= sum_k W^s2[k][p][s] U^s1[k][q][r]
+      // (B_ps X^s1_qr + X^s2_ps B_qr)
+      if (has[s1] || has[s2])
+        gemm22(h, -coef, W + 2 * s2 * blk, U + 2 * s1 * blk, c2_block(C2, s2, s1, s1, s2),
+               Dims2{{p, hh}, {hh, 1}, {c.st[0], c.st[3]}}, Dims2{{p, hh}, {hh, 1}, {c.st[1], c.st[2]}}, 1, ek, kk,
+               kk);
+    }
+  h.ws.put(U, capU);
+  h.ws.put(W, capW);
+}
+
+// C1[p,j] += coef sum_{q,r,s} V[p,q,r,s] D[r,s,q,j] on the excitation block
+// [P,H], D antisymmetric in its first two slots ([P,P,H,H]): the exchange
+// part equals the Coulomb part, so the sum is
+// 2 sum_{Q,r} B^Q_pr Y^Q_rj with Y^Q_rj = sum_{q,s} B^Q_qs D[r,s,q,j] (per spin).
+static void df_vd_onebody(Handle& h, const Tensor& D, Tensor& C1, double coef) {
+  const int p = h.na + h.nv, hh = h.nc + h.na, Q = h.naux;
+  if (p == 0 || hh == 0) return;
+  const long long n = h.n, n2 = n * n, P0 = h.nc, ph = (long long)p * hh;
+  const View& d = D.v;
+  size_t capY;
+  double* Y = h.ws.get((size_t)(2 * Q * ph), capY);
+  check_cuda(cudaMemsetAsync(Y, 0, (size_t)(2 * Q * ph) * sizeof(double), h.ws.stream), "memset");
+  bool has[2] = {false, false};
+  for (int sg = 0; sg < 2; ++sg)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int db = sg | s2 << 1 | s2 << 2 | sg << 3;  // D[r s, s s2, q s2, j s]
+      if (!((d.mask >> db) & 1)) continue;
+      has[sg] = true;
+      // Y^s[Q][r][j] += sum_{q in H, s in P} B[Q][q][P0+s] D[r,s,q,j]
+      const int ek[2] = {hh, p};
+      const long long ak[2] = {n, 1}, bk[2] = {d.st[2], d.st[1]};
+      gemm22(h, 1.0, h.B + P0, d.p + d.boff[db], Y + sg * Q * ph, Dims2{{1, Q}, {0, n2}, {0, ph}},
+             Dims2{{p, hh}, {d.st[0], d.st[3]}, {hh, 1}}, 2, ek, ak, bk);
+    }
+  const View& c = C1.v;
+  for (int sg = 0; sg < 2; ++sg) {
+    if (!has[sg]) continue;
+    const int cb = sg | sg << 1;
+    if (!((c.stored >> cb) & 1)) throw std::runtime_error("df term: spin block not stored");
+    C1.v.mask |= 1ULL << cb;
+    // C1^{ss}[p][j] += 2 coef sum_{Q,r} B[Q][P0+p][P0+r] Y^s[Q][r][j]
+    const int ek[2] = {Q, p};
+    const long long ak[2] = {n2, 1}, bk[2] = {ph, hh};
+    gemm22(h, 2.0 * coef, h.B + P0 * n + P0, Y + sg * Q * ph, c.p + c.boff[cb], Dims2{{1, p}, {0, n}, {0, c.st[0]}},
+           Dims2{{1, hh}, {0, 1}, {0, c.st[1]}}, 2, ek, ak, bk);
+  }
+  h.ws.put(Y, capY);
+}
+
+// ---------------------------------------------------------------------------
 // [X, T] into one output block pair (C1, C2)
 // ---------------------------------------------------------------------------
 // One-body operator c_f f1 + c_w (W1 + W1^+) as pieces: f1 on [G,G] and W1's
@@ -420,9 +588,12 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     contract(ws, 1.0, tmp.v, "qa", e.v, "ra", Mq, "qr");
     contract_x2(ws, 1.0, X2, "pqsr", Mq.v, "qr", C1, "ps");
   }
-  // [X2, T1] two-body
-  contract_x2(ws, 1.0, X2, "pqas", T1.v, "ar", C2, "pqrs");
-  contract_x2(ws, -1.0, X2, "pqar", T1.v, "as", C2, "pqrs");
+  // [X2, T1] two-body; on the excitation block the V part of the first two
+  // terms (three particle indices of V) in density-fitted form
+  const bool dfv = exc && df && X2.V && X2.cv != 0.0;
+  if (dfv) df_x2t1(h, T1, C2, X2.cv);
+  contract_x2(ws, 1.0, X2, "pqas", T1.v, "ar", C2, "pqrs", dfv);
+  contract_x2(ws, -1.0, X2, "pqar", T1.v, "as", C2, "pqrs", dfv);
   contract_x2(ws, 1.0, X2, "qirs", T1.v, "pi", C2, "pqrs");
   contract_x2(ws, -1.0, X2, "pirs", T1.v, "qi", C2, "pqrs");
   // [X2, T2] one-body with three single contractions
@@ -432,7 +603,8 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   // the memory peak of the large instances
   {
     Tensor D1 = dress(h, dress(h, dress(h, T2, 0, e), 1, e), 2, g);
-    contract_x2(ws, -0.5, X2, "pqrs", D1.v, "rsqj", C1, "pj");
+    if (dfv) df_vd_onebody(h, D1, C1, -0.5 * X2.cv);
+    contract_x2(ws, -0.5, X2, "pqrs", D1.v, "rsqj", C1, "pj", dfv);
   }
   {
     Tensor D2 = dress(h, dress(h, dress(h, T2, 0, g), 1, g), 2, e);
@@ -695,7 +867,9 @@ void issue_energy(Handle& h, bool pt3) {
   // Htilde(1) = 2 H(1) + [H(0), A(1)] (Eq. Hbar_1st); V on the classes the terms need
   Sym2 V;
   ws.tag = "build-v";
-  build_v(h, pt3 ? 0x1fu : (1u << 2), V);
+  // the [P,P,P,H] class is read only by terms evaluated in density-fitted
+  // form (df_x2t1, df_vd_onebody) and by small slabs of it: not stored
+  build_v(h, pt3 ? 0x0fu : (1u << 2), V, pt3);
   ws.tag = "E2";
   Tensor Xs1 = build_x1(h, 2.0, &W1, 1.0);
   Op2 Xs2{&V, 2.0, &W2, 1.0};

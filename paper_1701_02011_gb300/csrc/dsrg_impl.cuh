@@ -56,7 +56,7 @@ struct Handle {
 
 Tensor vclass(Handle& h, const Iv* ivs, double coef);
 Tensor build_x1(Handle& h, double c_v, const Tensor* W1, double c_w);
-void build_v(Handle& h, unsigned classes, Sym2& V);
+void build_v(Handle& h, unsigned classes, Sym2& V, bool on_demand = false);
 Tensor dress(Handle& h, const Tensor& X, int slot, const Tensor& M);
 Tensor dress(Handle& h, Tensor&& X, int slot, const Tensor& M);  // in place on a temporary
 void amplitudes(Handle& h, const Tensor* O1, const Tensor& O2, Tensor& T1, Tensor& T2, Tensor& W1, Tensor& W2);
