@@ -666,6 +666,51 @@ def run_cholesky(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_split_gemm(args, local_rank):
+    """One split-precision FP64 product C += A B (dsrg_split_gemm, the
+    contraction primitive of the mixed-precision path), M = N = K = --gemm-n,
+    Gaussian operands, --slices digit slices (default 8).  Packing of both
+    operands included.  Roofline: the tensor pipe against the measured bf16
+    peak, executed flops 2 n^3 S(S+1)/2 over the padded tiles."""
+    import numpy as np
+    import torch
+
+    import paper_1701_02011_gb300 as g
+    from paper_1701_02011_gb300 import build as libbuild
+
+    torch.cuda.set_device(local_rank)
+    libbuild.build()
+    n, S = args.gemm_n, args.slices or 8
+    rng = np.random.default_rng(0)
+    A = torch.from_numpy(rng.standard_normal((n, n))).cuda()
+    B = torch.from_numpy(rng.standard_normal((n, n))).cuda()
+    C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    for _ in range(max(args.warmup, 0)):
+        g.dsrg_split_gemm(A, B, C, 1.0, S)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.dsrg_split_gemm(A, B, C, 1.0, S)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms) / 1000.0
+    pad = lambda x, m: (x + m - 1) // m * m
+    executed = 2.0 * pad(n, 128) * pad(n, 64) * pad(n, 16) * S * (S + 1) / 2.0
+    line = {"metric": "split-precision FP64 product (M = N = K), packing included", "value": 2.0 * n ** 3 / t / 1e12,
+            "unit": "TFLOP/s (FP64 products computed)", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (split bf16 tensor-core products)", "data": "synthetic (Gaussian)",
+            "config": {"workload": "split_gemm", "n": n, "slices": S},
+            "roofline": {"bound": "tensor", "achieved": executed / t / 1e12, "peak": MEASURED_BF16, "unit": "TFLOP/s",
+                         "frac": executed / t / 1e12 / MEASURED_BF16, "traffic": None,
+                         "peak_source": MEASURED_BF16_SOURCE, "algorithmic": "executed bf16 flops"},
+            "gpu_launches": 3 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def _measured_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -692,11 +737,13 @@ def main(argv=None):
     ap.add_argument("--no-tune", action="store_true",
                     help="fixed tile/split rules for the split products (default: tuned in the first warm-up)")
     ap.add_argument("--workload", choices=("cas88_c30_v300_q1200", "cas66_c10_v100_q400", "cas44_c40_v500_q1800",
-                                           "scan32", "cas1616_c10_v100_q400", "cholesky_cas66"), default=WORKLOAD,
+                                           "scan32", "cas1616_c10_v100_q400", "cholesky_cas66", "split_gemm"),
+                    default=WORKLOAD,
                     help="CAS(8,8)/30 core/300 virtual (default), CAS(6,6)/10 core/100 virtual, "
                          "CAS(4,4)/40 core/500 virtual, the batched 32-point scan, a synthetic 16-orbital active "
-                         "space (10 core, 100 virtual), or the Cholesky factorisation of the CAS(6,6)-size "
-                         "two-electron supermatrix")
+                         "space (10 core, 100 virtual), the Cholesky factorisation of the CAS(6,6)-size "
+                         "two-electron supermatrix, or one split-precision product (--gemm-n)")
+    ap.add_argument("--gemm-n", type=int, default=4096, help="split_gemm: M = N = K")
     ap.add_argument("--scan-budget-gb", type=float, default=250.0,
                     help="device memory per scan batch (handles keep their captured buffers)")
     args = ap.parse_args(argv)
@@ -707,6 +754,8 @@ def main(argv=None):
         run_scan(args, rank, world, local_rank)
     elif args.workload == "cholesky_cas66":
         run_cholesky(args, rank, world, local_rank)
+    elif args.workload == "split_gemm":
+        run_split_gemm(args, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -268,12 +268,18 @@ bool split_faster(Workspace& ws, const GemmArgs& g) {
 
 // split-precision tensor-core path for every contraction with enough work
 // to pay for the operand slicing (about 40 us on the FP64 units); narrow
-// outputs use 32-column tiles, short ones split k over CTAs
+// outputs use 32-column tiles, short ones split k over CTAs.  With tuning,
+// products of 5e6 .. 5e7 flops, and products whose shorter output side is
+// at most 32 (where packing the long operand can cost more than the FP64
+// work) up to 1e11 flops, take whichever path was faster on their shape.
 bool split_route(Workspace& ws, const GemmArgs& g) {
   if (!(ws.slices > 0 && g.nbatch == 1 && g.K >= 32 && ozaki_supported(g))) return false;
   const double fl = 2.0 * (double)g.M * (double)g.N * (double)g.K;
+  const bool timed = ws.tune && g.A && g.B && g.C;
+  const long long nmin = g.M < g.N ? g.M : g.N;
+  if (timed && nmin <= 32 && fl >= 5e6 && fl < 1e11) return split_faster(ws, g);
   if (fl >= 5e7) return true;
-  if (!ws.tune || fl < 5e6 || !g.A || !g.B || !g.C) return false;
+  if (!timed || fl < 5e6) return false;
   return split_faster(ws, g);
 }
 

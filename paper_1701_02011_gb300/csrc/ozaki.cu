@@ -14,12 +14,15 @@
 namespace dsrg {
 namespace {
 
-// k per stage (a 64-byte row of bf16 digits), and stages per exact window:
-// a level sum over one window has at most 8 pairs x 128 products of
-// |d| <= 127, 8 x 128 x 127^2 < 2^24, so it is exact in FP32
-constexpr int OZ_BM = 128, OZ_BK = 32, OZ_WIN = 4;
+// k per stage (a 32-byte row of bf16 digits), stage buffers, and stages per
+// exact window: a level sum over one window has at most 8 pairs x 128
+// products of |d| <= 127, 8 x 128 x 127^2 < 2^24, so it is exact in FP32
+constexpr int OZ_BM = 128, OZ_BK = 16, OZ_NBUF = 4, OZ_WIN = 8;
+// row tiles per rasterisation group
+constexpr int OZ_GROUP = 8;
 constexpr int OZ_THREADS = 256;  // 8 warps: lane quadrant (warp % 4) x column half (warp / 4)
-constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // A stage tile of one slice: 4096 bf16 = 8 KiB
+constexpr int OZ_CTA_THREADS = OZ_THREADS + 32;  // and a ninth warp that issues the bulk copies
+constexpr int OZ_TILE_ELEMS = OZ_BM * OZ_BK;  // A stage tile of one slice: 2048 bf16 = 4 KiB
 constexpr int OZ_TILE_BYTES = OZ_TILE_ELEMS * 2;
 // exponents are stored as 2048 + frexp exponent of the row / column maximum (0: all zero)
 constexpr unsigned OZ_EBIAS = 2048;
@@ -32,16 +35,16 @@ __device__ int g_oz_status;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: K-major operand in the 64-byte swizzled
-// layout (rows of 32 bf16, 8-row groups 512 bytes apart; the 16-byte chunk c
-// of row r sits at chunk c ^ ((r >> 1) & 3)).
+// Shared-memory matrix descriptor: K-major operand in the 32-byte swizzled
+// layout (rows of 16 bf16, 8-row groups 256 bytes apart; the 16-byte chunk c
+// of row r sits at chunk c ^ ((r >> 2) & 1)).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
   d |= (uint64_t)1 << 16;                    // leading byte offset (unused when swizzled)
-  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)(256 >> 4) << 32;           // stride byte offset: 8 rows x 32 B
   d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)4 << 61;                    // 64-byte swizzle
+  d |= (uint64_t)6 << 61;                    // 32-byte swizzle
   return d;
 }
 
@@ -214,16 +217,56 @@ __device__ __forceinline__ double f32_to_f64_scaled(uint32_t u, int k) {
   return __longlong_as_double((long long)bits);
 }
 
-// One CTA: a 128 x BN tile of C with 8 warps; warp w reads TMEM lanes
-// 32 (w % 4) .. and column half w / 4.  The k range is walked in stages of
-// 32; two shared-memory buffers alternate, so the bulk copies of stage k + 1
-// run while the tensor cores work on stage k.  Every level c = t + u has its
-// own TMEM accumulator (S levels x BN columns); thread 0 issues all digit
-// pairs of a stage into them, and after every OZ_WIN stages (an exact window)
-// all warps fold the level sums, scaled by 2^(-7c), into float-float (hi, lo)
-// running sums held in registers.
+// barrier 1 over the 8 warps of the tile (the copy warp does not take part);
+// the _and form returns whether every thread's pred was true
+__device__ __forceinline__ void tile_sync() { asm volatile("bar.sync 1, %0;" ::"n"(OZ_THREADS) : "memory"); }
+__device__ __forceinline__ bool tile_sync_and(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "n"(OZ_THREADS)
+      : "memory");
+  return r != 0;
+}
+
+// Thread 0: every digit pair (t, u), t + u <= S + 1, of one stage into the
+// accumulator of level t + u.  For a fixed A slice t the levels
+// t + 1 .. S + 1 are adjacent in TMEM and the B slices 1 .. S + 1 - t adjacent
+// in shared memory, so one MMA of N = BN (S + 1 - t) columns (pieces of at
+// most 256) covers them and reads A_t once.  The first stage of a window
+// overwrites: the t = 1 MMAs cover every level.  descA0 / descB0 describe
+// the first A / B tile of buffer 0; boff is the buffer's byte offset (the
+// descriptors differ only in the start-address field, bytes / 16).
+template <int BN, int S>
+__device__ __forceinline__ void oz_issue_stage(uint32_t tm, uint64_t descA0, uint64_t descB0, uint32_t boff,
+                                               bool fresh) {
+  constexpr int B_TILE_BYTES = BN * OZ_BK * 2;
+  constexpr int UMAX = 256 / BN;
+  const uint64_t dA = descA0 + (boff >> 4), dB = descB0 + (boff >> 4);
+#pragma unroll
+  for (int t = 1; t <= S; ++t) {
+#pragma unroll
+    for (int u0 = 1; u0 <= S + 1 - t; u0 += UMAX) {
+      const int nu = (S + 1 - t) - u0 + 1 < UMAX ? (S + 1 - t) - u0 + 1 : UMAX;
+      mma_bf16(tm + (uint32_t)((t + u0 - 2) * BN), dA + (uint64_t)(((t - 1) * OZ_TILE_BYTES) >> 4),
+               dB + (uint64_t)(((u0 - 1) * B_TILE_BYTES) >> 4), oz_idesc(nu * BN), (fresh && t == 1) ? 0u : 1u);
+    }
+  }
+}
+
+// One CTA: a 128 x BN tile of C.  Warps 0-7: warp w reads TMEM lanes
+// 32 (w % 4) .. and column half w / 4; its thread 0 issues the MMAs.  Warp 8
+// (lane 0) issues the bulk copies.  The k range is walked in stages of 16;
+// four shared-memory buffers rotate: the copy warp refills a buffer as soon
+// as the MMAs of the stage that used it have completed, so copies run up to
+// three stages ahead of the tensor cores, and the MMA thread only waits for
+// data.  Every level c = t + u has its own TMEM accumulator (S levels x BN
+// columns); after every OZ_WIN stages (an exact window) warps 0-7 fold the
+// level sums, scaled by 2^(-7c), into float-float (hi, lo) running sums held
+// in registers.
 template <int BN>
-__global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
+__global__ void __launch_bounds__(OZ_CTA_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   constexpr uint32_t TMEM_COLS = 512;  // S <= 8 level accumulators of BN <= 64 columns
   constexpr int B_TILE_BYTES = BN * OZ_BK * 2;
   // columns per warp in the fold and epilogue: two column halves for BN >= 64;
@@ -233,18 +276,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   static_assert(8 * BN <= (int)TMEM_COLS, "TMEM columns");
   extern __shared__ unsigned char oz_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t bar_load[2], bar_mma[2], bar_win;
+  __shared__ uint64_t bar_load[OZ_NBUF], bar_mma[OZ_NBUF], bar_win;
   __shared__ uint32_t tmem_base;
   __shared__ long long colC[BN], rowC[OZ_BM];
   __shared__ int colE[BN];
+  __shared__ int issued[OZ_NBUF];  // copies issued per buffer (copy warp), read at the end
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32*quad.., columns half*HALF..
+  const bool copier = warp == OZ_THREADS / 32;
+  const int quad = warp & 3, half = (warp >> 2) & 1;  // TMEM lanes 32*quad.., columns half*HALF..
   const int row = quad * 32 + (tid & 31);
-  const int mt = blockIdx.x, nt = blockIdx.y, z = blockIdx.z;
+  // grouped rasterisation: consecutive CTAs walk the column tiles of a group
+  // of OZ_GROUP row tiles, so the CTAs running together share their A and B
+  // digit tiles in L2
+  int mt, nt;
+  {
+    const int lin = blockIdx.y * a.MT + blockIdx.x;
+    const int per = OZ_GROUP * a.NT;
+    const int first = (lin / per) * OZ_GROUP;
+    const int gm = a.MT - first < OZ_GROUP ? a.MT - first : OZ_GROUP;
+    const int within = lin - (lin / per) * per;
+    mt = first + within % gm;
+    nt = within / gm;
+  }
+  const int z = blockIdx.z;
   const int kt0 = a.splits > 1 ? z * a.ktper : 0;
   const int kt1 = a.splits > 1 ? (kt0 + a.ktper < a.KT ? kt0 + a.ktper : a.KT) : a.KT;
   const int S = a.S;
   const size_t stage_bytes = (size_t)S * (OZ_TILE_BYTES + B_TILE_BYTES);
+  const int ns = kt1 - kt0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -253,19 +312,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < OZ_NBUF; ++i) {
       mbar_init(&bar_load[i], 1);
       mbar_init(&bar_mma[i], 1);
+      issued[i] = 0;
     }
     mbar_init(&bar_win, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int t = tid; t < BN; t += OZ_THREADS) {
+  for (int t = tid; t < BN; t += OZ_CTA_THREADS) {
     long long n = (long long)nt * BN + t;
     colC[t] = n < a.N ? c_offset(n, a.nN, a.eN, a.cN) : -1;
     colE[t] = a.fb[(long long)nt * BN + t] - (int)OZ_EBIAS;
   }
-  for (int t = tid; t < OZ_BM; t += OZ_THREADS) {
+  for (int t = tid; t < OZ_BM; t += OZ_CTA_THREADS) {
     long long m = (long long)mt * OZ_BM + t;
     rowC[t] = m < a.M ? c_offset(m, a.nM, a.eM, a.cM) : -1;
   }
@@ -273,152 +333,135 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tm = tmem_base;
+  // matrix descriptors of the first A and B digit tiles of buffer 0; the
+  // others differ only in the start-address field (byte offset / 16)
+  const uint64_t descA0 = sdesc(smem_u32(smem));
+  const uint64_t descB0 = sdesc(smem_u32(smem + (size_t)S * OZ_TILE_BYTES));
+
+  // ---- copy warp: stage k (relative to kt0) into buffer k % OZ_NBUF, once
+  // the MMAs of stage k - OZ_NBUF (the buffer's last use) have completed
+  if (copier) {
+    if ((tid & 31) == 0) {
+      uint32_t ph_mma[OZ_NBUF] = {};
+      for (int k = 0; k < ns; ++k) {
+        const int b = k % OZ_NBUF, kt = kt0 + k;
+        if (k >= OZ_NBUF) {
+          if (!mbar_wait(&bar_mma[b], ph_mma[b], a.wait_cycles)) break;  // the MMA thread stopped
+          ph_mma[b] ^= 1;
+        }
+        unsigned char* base = smem + (size_t)b * stage_bytes;
+        mbar_expect_tx(&bar_load[b], (uint32_t)(S * (OZ_TILE_BYTES + B_TILE_BYTES)));
+        for (int s2 = 0; s2 < S; ++s2) {
+          bulk_g2s(base + (size_t)s2 * OZ_TILE_BYTES, a.As + ((size_t)(s2 * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS,
+                   OZ_TILE_BYTES, &bar_load[b]);
+          bulk_g2s(base + (size_t)S * OZ_TILE_BYTES + (size_t)s2 * B_TILE_BYTES,
+                   a.Bs + ((size_t)(s2 * a.NT + nt) * a.KT + kt) * (BN * OZ_BK), B_TILE_BYTES, &bar_load[b]);
+        }
+        issued[b] += 1;
+      }
+    }
+  }
+
+  // ---- warps 0-7: MMAs (thread 0), folds, epilogue
   const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   const uint32_t col0 = (uint32_t)(half * HALF);
-  const bool active = BN >= 64 || half == 0;
-
-  // running float-float sums of this thread's row and NCH x 32 columns
+  const bool active = !copier && (BN >= 64 || half == 0);
   uint32_t rhi[NCH][32], rlo[NCH][32];
 #pragma unroll
   for (int j = 0; j < NCH; ++j)
 #pragma unroll
     for (int q = 0; q < 32; ++q) rhi[j][q] = rlo[j][q] = 0u;
-
-  // thread 0 only: copies of stage k (relative to kt0) into buffer k & 1
-  auto issue_load = [&](int k) {
-    const int b = k & 1, kt = kt0 + k;
-    unsigned char* base = smem + (size_t)b * stage_bytes;
-    mbar_expect_tx(&bar_load[b], (uint32_t)(S * (OZ_TILE_BYTES + B_TILE_BYTES)));
-    for (int s = 0; s < S; ++s) {
-      bulk_g2s(base + (size_t)s * OZ_TILE_BYTES, a.As + ((size_t)(s * a.MT + mt) * a.KT + kt) * OZ_TILE_ELEMS,
-               OZ_TILE_BYTES, &bar_load[b]);
-      bulk_g2s(base + (size_t)S * OZ_TILE_BYTES + (size_t)s * B_TILE_BYTES,
-               a.Bs + ((size_t)(s * a.NT + nt) * a.KT + kt) * (BN * OZ_BK), B_TILE_BYTES, &bar_load[b]);
-    }
-  };
-  // thread 0 only: every digit pair (t, u), t + u <= S + 1, of stage k into
-  // the accumulator of level t + u.  For a fixed A slice t the levels
-  // t + 1 .. S + 1 are adjacent in TMEM and the B slices 1 .. S + 1 - t are
-  // adjacent in shared memory, so one MMA of N = BN (S + 1 - t) columns (in
-  // pieces of at most 256) covers them all and reads A_t once.  The first
-  // stage of a window overwrites: the t = 1 MMAs cover every level.
-  auto issue_mmas = [&](int k, bool fresh) {
-    const int b = k & 1;
-    unsigned char* base = smem + (size_t)b * stage_bytes;
-    constexpr int UMAX = 256 / BN;  // B slices per MMA
-    for (int t = 1; t <= S; ++t) {
-      const uint32_t aA = smem_u32(base + (size_t)(t - 1) * OZ_TILE_BYTES);
-      for (int u0 = 1; u0 <= S + 1 - t; u0 += UMAX) {
-        const int nu = (S + 1 - t) - u0 + 1 < UMAX ? (S + 1 - t) - u0 + 1 : UMAX;
-        const uint32_t d = tm + (uint32_t)((t + u0 - 2) * BN);
-        const uint32_t aB = smem_u32(base + (size_t)S * OZ_TILE_BYTES + (size_t)(u0 - 1) * B_TILE_BYTES);
-        const uint32_t idesc = oz_idesc(nu * BN);
-#pragma unroll
-        for (int ks = 0; ks < OZ_BK / 16; ++ks)
-          mma_bf16(d, sdesc(aA + 32 * ks), sdesc(aB + 32 * ks), idesc, (fresh && t == 1 && ks == 0) ? 0u : 1u);
-      }
-    }
-    mma_commit(&bar_mma[b]);
-  };
-
-  uint32_t ph_load[2] = {0, 0}, ph_mma[2] = {0, 0}, ph_win = 0;
-  bool load_pending[2] = {false, false}, mma_pending[2] = {false, false}, win_pending = false;  // thread 0
   bool ok = true;
-  const int ns = kt1 - kt0;
-  if (tid == 0 && ns > 0) {
-    issue_load(0);
-    load_pending[0] = true;
-  }
-  for (int k = 0; k < ns; ++k) {
-    const int b = k & 1;
-    const bool fresh = (k % OZ_WIN) == 0;
-    const bool wend = (k % OZ_WIN) == OZ_WIN - 1 || k == ns - 1;
-    if (tid == 0) {
-      if (ok) {
-        if (mbar_wait(&bar_load[b], ph_load[b], a.wait_cycles)) {
-          ph_load[b] ^= 1;
-          load_pending[b] = false;
-        } else {
-          ok = false;
+  int consumed[OZ_NBUF] = {};                  // thread 0: loads waited for per buffer
+  uint32_t ph_load[OZ_NBUF] = {}, ph_win = 0;  // thread 0 / every tile thread
+  bool win_pending = false;                    // thread 0
+  if (!copier) {
+    for (int k = 0; k < ns; ++k) {
+      const int b = k % OZ_NBUF;
+      const bool fresh = (k % OZ_WIN) == 0;
+      const bool wend = (k % OZ_WIN) == OZ_WIN - 1 || k == ns - 1;
+      if (tid == 0) {
+        if (ok) {
+          if (mbar_wait(&bar_load[b], ph_load[b], a.wait_cycles)) {
+            ph_load[b] ^= 1;
+            consumed[b] += 1;
+          } else {
+            ok = false;
+          }
+        }
+        if (ok) {
+          tc_fence_after();
+          switch (S) {
+            case 1: oz_issue_stage<BN, 1>(tm, descA0, descB0, (uint32_t)(b * stage_bytes), fresh); break;
+            case 2: oz_issue_stage<BN, 2>(tm, descA0, descB0, (uint32_t)(b * stage_bytes), fresh); break;
+            case 3: oz_issue_stage<BN, 3>(tm, descA0, descB0, (uint32_t)(b * stage_bytes), fresh); break;
+            case 4: oz_issue_stage<BN, 4>(tm, descA0, descB0, (uint32_t)(b * stage_bytes), fresh); break;
+            case 5: oz_issue_stage<BN, 5>(tm, descA0, descB0, (uint32_t)(b * stage_bytes), fresh); break;
+            case 6: oz_issue_stage<BN, 6>(tm, descA0, descB0, (uint32_t)(b * stage_bytes), fresh); break;
+            case 7: oz_issue_stage<BN, 7>(tm, descA0, descB0, (uint32_t)(b * stage_bytes), fresh); break;
+            default: oz_issue_stage<BN, 8>(tm, descA0, descB0, (uint32_t)(b * stage_bytes), fresh); break;
+          }
+          mma_commit(&bar_mma[b]);  // the buffer is free once these complete
+        }
+        if (wend) {  // completes once every MMA issued so far has completed
+          mma_commit(&bar_win);
+          win_pending = true;
         }
       }
-      if (ok) {
-        tc_fence_after();
-        issue_mmas(k, fresh);
-        mma_pending[b] = true;
-        // the other buffer is free once the MMAs of stage k - 1 completed
-        if (k + 1 < ns) {
-          const int b1 = (k + 1) & 1;
-          if (mma_pending[b1]) {
-            if (mbar_wait(&bar_mma[b1], ph_mma[b1], a.wait_cycles)) {
-              ph_mma[b1] ^= 1;
-              mma_pending[b1] = false;
-            } else {
-              ok = false;
+      if (!wend) continue;
+      const bool w = mbar_wait(&bar_win, ph_win, a.wait_cycles);
+      if (w) ph_win ^= 1;
+      if (tid == 0 && w) win_pending = false;
+      ok = tile_sync_and(ok && w);
+      tc_fence_after();
+      if (!ok) break;
+      // fold the window: (hi, lo) += acc_c * 2^(-7c), two-sum in paired FP32
+      if (active) {
+        for (int c = 2; c <= S + 1; ++c) {
+          const float scale = exp2f(-7.0f * (float)c);
+          const uint64_t sc2 = f2_pack(__float_as_uint(scale), __float_as_uint(scale));
+#pragma unroll
+          for (int j = 0; j < NCH; ++j) {
+            uint32_t acc[32];
+            tmem_ld32(tm + lane_off + (uint32_t)((c - 2) * BN) + col0 + 32 * j, acc);
+            tmem_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 32; q += 2) {
+              const uint64_t x = f2_mul(f2_pack(acc[q], acc[q + 1]), sc2);
+              const uint64_t h = f2_pack(rhi[j][q], rhi[j][q + 1]);
+              const uint64_t s_ = f2_add(h, x);
+              const uint64_t bp = f2_sub(s_, h);
+              const uint64_t err = f2_add(f2_sub(h, f2_sub(s_, bp)), f2_sub(x, bp));
+              uint64_t l = f2_add(f2_pack(rlo[j][q], rlo[j][q + 1]), err);
+              const uint64_t s2 = f2_add(s_, l);
+              l = f2_sub(l, f2_sub(s2, s_));
+              f2_unpack(s2, rhi[j][q], rhi[j][q + 1]);
+              f2_unpack(l, rlo[j][q], rlo[j][q + 1]);
             }
           }
-          if (ok) {
-            issue_load(k + 1);
-            load_pending[b1] = true;
-          }
         }
       }
-      if (wend) {  // completes once every MMA issued so far has completed
-        mma_commit(&bar_win);
-        win_pending = true;
-      }
+      // the accumulators are read; the next window may overwrite them
+      tc_fence_before();
+      tile_sync();
+      tc_fence_after();
     }
-    if (!wend) continue;
-    const bool w = mbar_wait(&bar_win, ph_win, a.wait_cycles);
-    if (w) ph_win ^= 1;
-    if (tid == 0 && w) win_pending = false;
-    ok = __syncthreads_and(ok && w) != 0;
-    tc_fence_after();
-    if (!ok) break;
-    // fold the window: (hi, lo) += acc_c * 2^(-7c), two-sum in paired FP32
-    if (active) {
-      for (int c = 2; c <= S + 1; ++c) {
-        const float scale = exp2f(-7.0f * (float)c);
-        const uint64_t sc2 = f2_pack(__float_as_uint(scale), __float_as_uint(scale));
-#pragma unroll
-        for (int j = 0; j < NCH; ++j) {
-          uint32_t acc[32];
-          tmem_ld32(tm + lane_off + (uint32_t)((c - 2) * BN) + col0 + 32 * j, acc);
-          tmem_wait_ld();
-#pragma unroll
-          for (int q = 0; q < 32; q += 2) {
-            const uint64_t x = f2_mul(f2_pack(acc[q], acc[q + 1]), sc2);
-            const uint64_t h = f2_pack(rhi[j][q], rhi[j][q + 1]);
-            const uint64_t s_ = f2_add(h, x);
-            const uint64_t bp = f2_sub(s_, h);
-            const uint64_t err = f2_add(f2_sub(h, f2_sub(s_, bp)), f2_sub(x, bp));
-            uint64_t l = f2_add(f2_pack(rlo[j][q], rlo[j][q + 1]), err);
-            const uint64_t s2 = f2_add(s_, l);
-            l = f2_sub(l, f2_sub(s2, s_));
-            f2_unpack(s2, rhi[j][q], rhi[j][q + 1]);
-            f2_unpack(l, rlo[j][q], rlo[j][q + 1]);
-          }
-        }
-      }
-    }
-    // the accumulators are read; the next window may overwrite them
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
   }
-  // after a timed-out wait: give the copies and MMAs still in flight a second
-  // bounded wait (the fixed default budget) before the shared memory and TMEM
-  // are released
+  // every warp: the copy warp's count of issued copies is visible after this
+  __syncthreads();
+  // after a timed-out wait: wait once more (the fixed default budget) for
+  // copies issued but not consumed and for every MMA issued, before the
+  // shared memory and TMEM are released
   if (!ok && tid == 0) {
-    for (int i = 0; i < 2; ++i)
-      if (load_pending[i]) mbar_wait(&bar_load[i], ph_load[i], OZ_WAIT_CYCLES);
+    for (int i = 0; i < OZ_NBUF; ++i)
+      if (issued[i] > consumed[i]) mbar_wait(&bar_load[i], ph_load[i], OZ_WAIT_CYCLES);
     if (win_pending) mbar_wait(&bar_win, ph_win, OZ_WAIT_CYCLES);
   }
   // epilogue: the scaled tile 2^(ea[m] + fb[n]) (hi + lo) goes to shared
-  // memory (the stage buffers are free once the last MMA has completed; rows
-  // padded by one double against bank conflicts), then consecutive threads
-  // write consecutive columns of C (alpha times, accumulated) or of the
-  // split-k partial part[z]
+  // memory (the stage buffers are free once the last MMA has completed and
+  // every copy was consumed; rows padded by one double against bank
+  // conflicts), then consecutive threads write consecutive columns of C
+  // (alpha times, accumulated) or of the split-k partial part[z]
   constexpr int LDT = BN + 1;
   double* stile = reinterpret_cast<double*>(smem);
   if (ok && active) {
@@ -434,7 +477,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_mma(const OzArgs a) {
     }
   }
   __syncthreads();
-  if (ok) {
+  if (ok && !copier) {
     if (a.splits > 1) {
       const long long ldp = (long long)a.NT * BN;
       double* pz = a.part + ((long long)z * a.MT * OZ_BM + (long long)mt * OZ_BM) * ldp + (long long)nt * BN;
@@ -702,8 +745,8 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
       }
     }
     const unsigned tr = r / p.TR, rr = r - tr * p.TR;  // TR is 32, 64 or 128
-    const int tk = (int)(q >> 2), chunk = (int)(q & 3);   // four 8-element chunks per 32-k row
-    const long long within = (long long)rr * OZ_BK + ((chunk ^ ((rr >> 1) & 3)) << 3);
+    const int tk = (int)(q >> 1), chunk = (int)(q & 1);   // two 8-element chunks per 16-k row
+    const long long within = (long long)rr * OZ_BK + ((chunk ^ ((rr >> 2) & 1)) << 3);
 #pragma unroll
     for (int t = 1; t <= S; ++t) {
       uint32_t w[4];
@@ -747,7 +790,7 @@ inline int oz_grid(long long n) {
 }
 
 size_t oz_smem_bytes(int S, int BN) {
-  const size_t tiles = 2 * ((size_t)S * OZ_TILE_BYTES + (size_t)S * BN * OZ_BK * 2);  // two stage buffers
+  const size_t tiles = OZ_NBUF * ((size_t)S * OZ_TILE_BYTES + (size_t)S * BN * OZ_BK * 2);  // stage buffers
   const size_t stage = (size_t)OZ_BM * (BN + 1) * sizeof(double);  // epilogue tile
   return (tiles > stage ? tiles : stage) + 1024;
 }
@@ -773,7 +816,7 @@ void oz_launch_bn(const OzArgs& a, int MT, int NT, cudaStream_t st) {
   size_t smem = oz_smem_bytes(a.S, BN);
   if (smem < 120 * 1024) smem = 120 * 1024;
   oz_smem_attribute<BN>();
-  k_ozaki_mma<BN><<<dim3(MT, NT, a.splits > 1 ? a.splits : 1), OZ_THREADS, smem, st>>>(a);
+  k_ozaki_mma<BN><<<dim3(MT, NT, a.splits > 1 ? a.splits : 1), OZ_CTA_THREADS, smem, st>>>(a);
   if (a.splits > 1) {
     // few outputs, many splits: a warp per output keeps loads in flight
     if (a.splits >= 32 && a.M * a.N < 152LL * 256)
@@ -889,10 +932,10 @@ void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoic
   // spread a short output over more CTAs by splitting the k tiles
   int splits = 1, ktper = KT;
   const long long ctas = (long long)MT * NT;
-  if (ch.split_mode != 1 && ctas < 2 * 152 && KT >= 8) {
+  if (ch.split_mode != 1 && ctas < 2 * 152 && KT >= 2 * OZ_WIN) {
     long long sp = (2 * 152 + ctas - 1) / ctas;
     if (ch.split_mode == 2) sp *= 2;
-    if (sp > KT / 4) sp = KT / 4;
+    if (sp > KT / OZ_WIN) sp = KT / OZ_WIN;  // at least one exact window per split
     if (sp >= 2) {
       ktper = (KT + (int)sp - 1) / (int)sp;
       splits = (KT + ktper - 1) / ktper;
@@ -1044,7 +1087,7 @@ OzChoice choose(Workspace& ws, const GemmArgs& g0, int S, int kind) {
     if (bn != 32 && bn / 2 >= nshort) continue;
     const long long big = g0.M > g0.N ? g0.M : g0.N;
     const long long ctas = ((big + OZ_BM - 1) / OZ_BM) * ((nshort + bn - 1) / bn);
-    const bool splits = ctas < 2 * 152 && KT >= 8;
+    const bool splits = ctas < 2 * 152 && KT >= 2 * OZ_WIN;
     for (int sm = 0; sm < (splits ? 3 : 1); ++sm) {
       OzChoice c;
       c.bn = bn;
