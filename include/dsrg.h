@@ -258,11 +258,13 @@ int dsrg_cholesky(long long N, const double *V, double tau, int max_vecs, double
  *   C[m][n] += alpha * sum_k A[m][k] B[k][n]
  * A [M][K] (row stride lda), B [K][N] (row stride ldb), C [M][N] (row stride
  * ldc), all FP64 device memory, row-major.  Every row of A and column of B is
- * scaled by a power of two and cut into `slices` (1..8) signed 7-bit digits
- * held exactly in BF16; digit products are accumulated exactly in FP32 over
- * 64-long chunks of k by tcgen05.mma and added into a two-float running sum,
- * so the result carries about 7*slices bits relative to the product of the
- * row and column maxima (Ozaki et al., Numer. Algorithms 59 (2012) 95).
+ * scaled by a power of two, rounded to a grid of 2^(7*slices - 1) steps and
+ * cut into `slices` (1..8) balanced base-128 digits (|d| <= 64) held exactly
+ * in BF16; digit products are accumulated exactly in FP32 over 480-long
+ * windows of k by tcgen05.mma and added into a two-float running sum, so the
+ * result carries about 7*slices bits relative to the product of the row and
+ * column maxima (Ozaki et al., Numer. Algorithms 59 (2012) 95).  With one
+ * slice, integers |x| <= 63 are held exactly.
  * Scratch is allocated and released inside the call; synchronises `stream`.
  * Errors: DSRG_ERR_ARG (sizes >= 2^31, slices, NULL), DSRG_ERR_OOM (scratch),
  * DSRG_ERR_CUDA (launch failure), DSRG_ERR_TIMEOUT (a bounded wait inside the

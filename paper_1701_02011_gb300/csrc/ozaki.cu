@@ -15,9 +15,12 @@ namespace dsrg {
 namespace {
 
 // k per stage (a 32-byte row of bf16 digits), stage buffers, and stages per
-// exact window: a level sum over one window has at most 8 pairs x 128
-// products of |d| <= 127, 8 x 128 x 127^2 < 2^24, so it is exact in FP32
-constexpr int OZ_BM = 128, OZ_BK = 16, OZ_NBUF = 4, OZ_WIN = 8;
+// exact window: digits are balanced, |d| <= 64, so a level sum over one
+// window has at most 8 pairs x 480 products of |d d'| <= 2^12,
+// 8 x 480 x 4096 < 2^24, and is exact in FP32
+constexpr int OZ_BM = 128, OZ_BK = 16, OZ_NBUF = 4, OZ_WIN = 30;
+// fewest stages per k split
+constexpr int OZ_SPLIT_MIN = 8;
 // row tiles per rasterisation group
 constexpr int OZ_GROUP = 8;
 constexpr int OZ_THREADS = 256;  // 8 warps: lane quadrant (warp % 4) x column half (warp / 4)
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(OZ_CTA_THREADS, 1) k_ozaki_mma(const OzArgs a)
       const int cc = (int)col0 + 32 * j;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const int k = em + colE[cc + q];
+        const int k = em + colE[cc + q] + 2;  // x = 2^(e + 1) sum_t d_t 2^(-7t) on both sides
         stile[row * LDT + cc + q] = f32_to_f64_scaled(rhi[j][q], k) + f32_to_f64_scaled(rlo[j][q], k);
       }
     }
@@ -580,7 +583,7 @@ struct OzPack {
 // the row index).
 //   pass 1: eu[r] = 2048 + max over k of the binary exponent ex with
 //           |x| < 2^ex (frexp), 0 for an all-zero row (eu zeroed beforehand);
-//   pass 2: the S signed 7-bit digits of x 2^(-e) go to the swizzled tiles,
+//   pass 2: the S balanced 7-bit digits of x 2^(-e) go to the swizzled tiles,
 //           eight bf16 (16 bytes) per store.
 constexpr int PACK_T = 256;
 
@@ -699,8 +702,11 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const PackPass pp) {
   }
 }
 
-// S digits of 7 bits of each element (sign and magnitude), bf16 encodings of
-// the magnitudes 0..127 from a shared table
+// S balanced base-128 digits of each element: V = round(x 2^(7S - 1 - e)),
+// |V| <= 2^(7S - 1) (|x| < 2^e, e the row / column exponent), written as
+// V = sum_t d_t 128^(S - t) with |d_t| <= 64, so x = 2^(e + 1) sum_t d_t 2^(-7t);
+// the digits are extracted from the lowest up with balanced remainders and
+// stored as bf16 (magnitudes 0..64 from a shared table, sign bit set)
 template <int S>
 __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
   const int o = blockIdx.y;
@@ -710,11 +716,11 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
   const int kfast = pp.kfast[o];
   const FastDiv fQ = pp.fQ[o], fR = pp.fR[o];
   const unsigned W = pp.W[o];
-  __shared__ uint32_t bf[128];
-  if (threadIdx.x < 128) bf[threadIdx.x] = __float_as_uint((float)threadIdx.x) >> 16;  // exact for 0..127
+  __shared__ uint32_t bf[65];
+  if (threadIdx.x < 65) bf[threadIdx.x] = __float_as_uint((float)threadIdx.x) >> 16;  // exact for 0..64
   __syncthreads();
   const long long tile_elems = (long long)p.TR * OZ_BK;
-  constexpr int F = 7 * S;
+  constexpr int F = 7 * S - 1;
   const unsigned stride = gridDim.x * PACK_T;
   for (unsigned i = blockIdx.x * PACK_T + threadIdx.x; i < W; i += stride) {
     unsigned r, q;
@@ -722,14 +728,12 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
     long long x[8];
     pack_load8(p, r, q, x);
     const int e = r < (unsigned long long)p.R ? (int)eu[r] - (int)OZ_EBIAS : 0;
-    unsigned long long v[8];
-    unsigned neg = 0;
+    int dg[S][8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      v[j] = 0;
+      long long V = 0;
       const long long bits = x[j];
       if ((bits << 1) != 0) {
-        if (bits < 0) neg |= 1u << j;
         const int be = (int)((bits >> 52) & 0x7FF);
         unsigned long long m = (unsigned long long)(bits & ((1LL << 52) - 1));
         int E;
@@ -739,10 +743,20 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
         } else {
           E = -1074;
         }
-        const int sh_ = E + F - e;  // v = m 2^sh < 2^F
-        if (sh_ >= 0) v[j] = sh_ < 12 ? (m << sh_) : 0;
-        else v[j] = (-sh_) >= 64 ? 0 : (m >> (-sh_));
+        const int sh_ = E + F - e;  // |x| 2^(F - e) = m 2^sh < 2^F
+        unsigned long long v;
+        if (sh_ >= 0) v = sh_ < 12 ? (m << sh_) : 0;
+        else if (-sh_ >= 64) v = 0;
+        else v = (m >> (-sh_)) + ((m >> (-sh_ - 1)) & 1ULL);  // to nearest, ties away from zero
+        V = bits < 0 ? -(long long)v : (long long)v;
       }
+#pragma unroll
+      for (int t = S; t >= 2; --t) {
+        const long long d = ((V + 64) & 127) - 64;
+        dg[t - 1][j] = (int)d;
+        V = (V - d) >> 7;
+      }
+      dg[0][j] = (int)V;  // |V| <= 64 here
     }
     const unsigned tr = r / p.TR, rr = r - tr * p.TR;  // TR is 32, 64 or 128
     const int tk = (int)(q >> 1), chunk = (int)(q & 1);   // two 8-element chunks per 16-k row
@@ -755,10 +769,9 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
         uint32_t pair = 0;
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          const int j = 2 * h + u;
-          const uint32_t mag = (uint32_t)(v[j] >> (7 * (S - t))) & 127u;
-          const uint32_t sgn = (neg >> j & 1u) && mag ? 0x8000u : 0u;
-          pair |= (bf[mag] | sgn) << (16 * u);
+          const int d = dg[t - 1][2 * h + u];
+          const uint32_t mag = min((uint32_t)(d < 0 ? -d : d), 64u);  // |d| <= 64 by construction
+          pair |= (bf[mag] | (d < 0 ? 0x8000u : 0u)) << (16 * u);
         }
         w[h] = pair;
       }
@@ -932,10 +945,10 @@ void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoic
   // spread a short output over more CTAs by splitting the k tiles
   int splits = 1, ktper = KT;
   const long long ctas = (long long)MT * NT;
-  if (ch.split_mode != 1 && ctas < 2 * 152 && KT >= 2 * OZ_WIN) {
+  if (ch.split_mode != 1 && ctas < 2 * 152 && KT >= 2 * OZ_SPLIT_MIN) {
     long long sp = (2 * 152 + ctas - 1) / ctas;
     if (ch.split_mode == 2) sp *= 2;
-    if (sp > KT / OZ_WIN) sp = KT / OZ_WIN;  // at least one exact window per split
+    if (sp > KT / OZ_SPLIT_MIN) sp = KT / OZ_SPLIT_MIN;
     if (sp >= 2) {
       ktper = (KT + (int)sp - 1) / (int)sp;
       splits = (KT + ktper - 1) / ktper;
@@ -1087,7 +1100,7 @@ OzChoice choose(Workspace& ws, const GemmArgs& g0, int S, int kind) {
     if (bn != 32 && bn / 2 >= nshort) continue;
     const long long big = g0.M > g0.N ? g0.M : g0.N;
     const long long ctas = ((big + OZ_BM - 1) / OZ_BM) * ((nshort + bn - 1) / bn);
-    const bool splits = ctas < 2 * 152 && KT >= 2 * OZ_WIN;
+    const bool splits = ctas < 2 * 152 && KT >= 2 * OZ_SPLIT_MIN;
     for (int sm = 0; sm < (splits ? 3 : 1); ++sm) {
       OzChoice c;
       c.bn = bn;

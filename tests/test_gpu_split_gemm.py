@@ -19,13 +19,14 @@ def lib():
 
 
 def test_one_slice_is_exact_on_small_integers(lib):
-    """|a|, |b| <= 127: one 7-bit digit holds every element exactly, so the
-    product must be exact (ragged M, N, K across 128/128/64 tiles)."""
+    """|a|, |b| <= 63: one balanced 7-bit digit (|d| <= 64 on the grid of
+    the row/column exponent, 2^6 for a maximum of 63) holds every element
+    exactly, so the product must be exact (ragged M, N, K across tiles)."""
     import torch
     rng = np.random.default_rng(1)
     M, N, K = 200, 150, 300
-    A = rng.integers(-127, 128, (M, K)).astype(np.float64)
-    B = rng.integers(-127, 128, (K, N)).astype(np.float64)
+    A = rng.integers(-63, 64, (M, K)).astype(np.float64)
+    B = rng.integers(-63, 64, (K, N)).astype(np.float64)
     ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
     C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
     lib.dsrg_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 1.0, 1)
@@ -54,8 +55,8 @@ def test_tile_shapes_orientation_and_k_split(lib, M, N, K):
     split over CTAs, and ragged edges; exact on small integers with one slice."""
     import torch
     rng = np.random.default_rng(M + N + K)
-    A = rng.integers(-127, 128, (M, K)).astype(np.float64)
-    B = rng.integers(-127, 128, (K, N)).astype(np.float64)
+    A = rng.integers(-63, 64, (M, K)).astype(np.float64)
+    B = rng.integers(-63, 64, (K, N)).astype(np.float64)
     ref = (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64)
     C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
     lib.dsrg_split_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C, 1.0, 1)
@@ -65,9 +66,9 @@ def test_tile_shapes_orientation_and_k_split(lib, M, N, K):
 @pytest.mark.parametrize("slices,lo,hi", [(2, 1e-10, 2.0 ** -10), (3, 1e-12, 2.0 ** -17)])
 def test_few_slices_truncate_visibly(lib, slices, lo, hi):
     """With 2 or 3 digit slices the product carries about 7 S bits relative to
-    the row/column maxima: its error against FP64 must exceed FP64 rounding by
+    the row/column maxima (each operand rounded to a 2^(7 S - 1) grid): its error against FP64 must exceed FP64 rounding by
     orders of magnitude (so an FP64 fallback would fail here) and stay within
-    the digit-truncation bound."""
+    the digit-rounding bound."""
     import torch
     rng = np.random.default_rng(5)
     M, N, K = 300, 200, 500
