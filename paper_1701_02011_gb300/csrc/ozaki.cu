@@ -573,8 +573,23 @@ struct OzPack {
   int T, KT;           // tiles along rows (TR each) and k (64 each)
   int TR;              // rows per tile: 128 (A) or BN (B)
   int S;
+  int vec;             // 1: every full 8-group is 64 contiguous, 16-byte aligned bytes
   FastDiv fR[4], fK[4];  // divisors of eR, eK
 };
+
+// whether pack_load8 may read a full k group with 16-byte loads: unit
+// innermost k stride, groups that never cross a carry of the k multi-index
+// (innermost extent a multiple of 8), every other stride even and the base
+// 16-byte aligned, so every group starts on a 16-byte boundary
+inline int pack_vec_ok(const OzPack& p) {
+  if (p.nK < 1 || p.sK[p.nK - 1] != 1 || p.eK[p.nK - 1] % 8 != 0) return 0;
+  if (reinterpret_cast<uintptr_t>(p.src) % 16 != 0) return 0;
+  for (int d = 0; d < p.nK - 1; ++d)
+    if (p.sK[d] % 2 != 0) return 0;
+  for (int d = 0; d < p.nR; ++d)
+    if (p.sR[d] % 2 != 0) return 0;
+  return 1;
+}
 
 // Operand preparation runs in two passes over the padded operand viewed as
 // rows x (8-element k groups).  Work item i is one (row r, group q); when the
@@ -636,6 +651,16 @@ __device__ __forceinline__ void pack_load8(const OzPack& p, unsigned r, unsigned
       lin = qd;
     }
   }
+  if (p.vec && k0 + 8 <= (unsigned long long)p.K) {
+    const longlong2* v = reinterpret_cast<const longlong2*>(src + roff + off);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const longlong2 t = v[h];
+      x[2 * h] = t.x;
+      x[2 * h + 1] = t.y;
+    }
+    return;
+  }
   const int last = p.nK - 1;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -665,6 +690,10 @@ struct PackPass {
   unsigned W[2];
 };
 
+// Each CTA walks one contiguous range of work items, 256 at a time, and each
+// thread keeps the maximum of its current row in a register, flushed by an
+// atomic max when its row changes and at the end: a few long rows (a short
+// side of 8 or 38) would otherwise send millions of atomics to a few words.
 __global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const PackPass pp) {
   const int o = blockIdx.y;
   const OzPack& p = pp.p[o];
@@ -672,33 +701,40 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const PackPass pp) {
   const int kfast = pp.kfast[o];
   const FastDiv fQ = pp.fQ[o], fR = pp.fR[o];
   const unsigned W = pp.W[o];
-  const unsigned stride = gridDim.x * PACK_T;
-  for (unsigned base = blockIdx.x * PACK_T; base < W; base += stride) {
-    const unsigned i = base + threadIdx.x;
+  const unsigned long long span = (unsigned long long)gridDim.x * PACK_T;
+  const unsigned long long per = (W + span - 1) / span * PACK_T;  // items per CTA
+  const unsigned long long lo = blockIdx.x * per;
+  const unsigned long long hi = lo + per < W ? lo + per : W;
+  long long held = -1;  // row whose maximum is in hv
+  unsigned hv = 0;
+  for (unsigned long long base = lo; base < hi; base += PACK_T) {
+    if (base + threadIdx.x >= hi) break;
+    const unsigned i = (unsigned)(base + threadIdx.x);
+    unsigned rr, q;
+    pack_item(i, fQ, fR, kfast != 0, rr, q);
+    if (rr >= (unsigned long long)p.R) continue;
+    long long x[8];
+    pack_load8(p, rr, q, x);
     unsigned v = 0;
-    long long r = -1;
-    if (i < W) {
-      unsigned rr, q;
-      pack_item(i, fQ, fR, kfast != 0, rr, q);
-      if (rr < (unsigned long long)p.R) {
-        long long x[8];
-        pack_load8(p, rr, q, x);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const unsigned c = exp_code(x[j]);
-          v = c > v ? c : v;
-        }
-        r = rr;
-      }
+    for (int j = 0; j < 8; ++j) {
+      const unsigned c = exp_code(x[j]);
+      v = c > v ? c : v;
     }
-    // one atomic per warp when the whole warp works on one row
-    const long long r0 = __shfl_sync(0xffffffffu, r, 0);
-    if (__all_sync(0xffffffffu, r == r0)) {
-      v = __reduce_max_sync(0xffffffffu, v);
-      if ((threadIdx.x & 31) == 0 && r0 >= 0 && v) atomicMax(eu + r0, v);
-    } else if (r >= 0 && v) {
-      atomicMax(eu + r, v);
+    if ((long long)rr != held) {
+      if (held >= 0 && hv) atomicMax(eu + held, hv);
+      held = rr;
+      hv = 0;
     }
+    hv = v > hv ? v : hv;
+  }
+  // final flush: one atomic per warp when every lane holds the same row
+  const long long r0 = __shfl_sync(0xffffffffu, held, 0);
+  if (__all_sync(0xffffffffu, held == r0)) {
+    const unsigned m = __reduce_max_sync(0xffffffffu, hv);
+    if ((threadIdx.x & 31) == 0 && r0 >= 0 && m) atomicMax(eu + r0, m);
+  } else if (held >= 0 && hv) {
+    atomicMax(eu + held, hv);
   }
 }
 
@@ -929,6 +965,8 @@ void ozaki_run(Workspace& ws, const GemmArgs& g0, int S, int kind, const OzChoic
       a.cN[d] = g0.cM[d];
     }
   }
+  pa.vec = pack_vec_ok(pa);
+  pb.vec = pack_vec_ok(pb);
   int BN = ch.bn ? ch.bn : N <= 32 ? 32 : 64;
   // shared memory per CTA is capped at 227 KiB (static arrays take up to 4 KiB)
   while (BN > 32 && oz_smem_bytes(S, BN) + 4096 > 227 * 1024) BN /= 2;

@@ -7,7 +7,7 @@
   The test regenerates the seeded input and checks it against the recorded
   fingerprints first, so both sides see the same problem.
 * CAS(8,8), 30 core, 300 virtual, 1200 auxiliary (the mixed-precision
-  workload, too large for the oracle): the split path with 8 digit slices
+  workload, too large for the oracle): the split path with 7 digit slices
   against the FP64 path, every component within 1e-6 Eh, in the launch
   configuration the benchmark times.
 """
@@ -77,7 +77,7 @@ def test_cas66_fp64_and_split_against_oracle(lib):
 def test_cas88_split_against_fp64(lib):
     inst = synth.config_instance("cas88_c30_v300_q1200")
     dev = _device(inst)
-    h = lib.Dsrg(dev, precision=lib.DSRG_PREC_SPLIT, slices=8, tune=True)
+    h = lib.Dsrg(dev, precision=lib.DSRG_PREC_SPLIT, slices=7, tune=True)
     try:
         es = h.pt3()
     finally:
