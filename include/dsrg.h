@@ -129,6 +129,38 @@ int dsrg_pt2(dsrg_handle *h, dsrg_energies *out);
 /* E(2) and E(3) components.  Synchronises the handle's stream. */
 int dsrg_pt3(dsrg_handle *h, dsrg_energies *out);
 
+typedef struct {
+  double e2, e3a, e3b, e3;  /* the unrelaxed components, as dsrg_pt3          */
+  double e_relaxed2;        /* one-step relaxed DSRG-MRPT2 energy, relative
+                               to E0 (lowest eigenvalue of Hbar^[2])         */
+  double e_relaxed3;        /* one-step relaxed DSRG-MRPT3 energy, relative
+                               to E0 (lowest eigenvalue of Hbar^[3])         */
+  double residual2, residual3; /* |H x - e x| of the unit eigenvector found */
+  long long ndet;           /* determinants of the CI space                  */
+  int steps2, steps3;       /* Lanczos steps taken                           */
+} dsrg_relaxed_energies;
+
+/*
+ * One-step relaxed energies (paper Eq. E_relaxed with Eq. energy_relaxed;
+ * App. A).  Evaluates the PT3 energy and, on the way, the all-active blocks
+ * of the summed transformed Hamiltonian Hbar^[k]_{1,2} (k = 2: H^(0) + H^(1)
+ * + 1/2 [Htilde(1), A(1)]; k = 3: plus 1/2 [Htilde(1), A(2)] +
+ * 1/2 [Htilde(2), A(1)]); folds the core and rewrites the operator in
+ * true-vacuum order with the reference's gamma1 and lambda2 (App. A), builds
+ * its matrix over the determinants with n_alpha and n_beta electrons in the
+ * na active orbitals, and returns the lowest eigenvalue of each (Lanczos on
+ * the GPU).  E0 needs the bare integrals, which are not inputs: every energy
+ * is relative to it, so e_relaxedk - (e2 [+ e3]) is the relaxation energy.
+ * The active-space part of H^(0) is the given Fock diagonal.  The reference's
+ * densities must be those of a state with n_alpha, n_beta active electrons
+ * (no check is made).  Synchronises the handle's stream; drops a captured
+ * batch graph as dsrg_pt3 does.
+ * Errors: DSRG_ERR_ARG (out NULL, n_alpha or n_beta outside [0, na], more
+ * than 20000 determinants), DSRG_ERR_STATE (NULL handle), otherwise as
+ * dsrg_pt3.  Ownership: the caller keeps out.
+ */
+int dsrg_relaxed(dsrg_handle *h, int n_alpha, int n_beta, dsrg_relaxed_energies *out);
+
 /*
  * PT3 energies of n independent instances (the points of a potential-energy
  * scan, any sizes), all in flight at once: handle i's energy runs on its own
@@ -283,6 +315,11 @@ int dsrg_split_gemm(long long M, long long N, long long K, const double *A, long
  *   "T1b" [2p][2h], "T2b" [2p][2p][2h][2h]     second-order amplitudes
  *   "O1" [2p][2h], "O2" [2p][2p][2h][2h]       excitation blocks of
  *                                              1/2 [Htilde(1), A(1)]_{1,2}
+ *   "Hbar1_2" [2na][2na], "Hbar2_2" [2na]^4    all-active blocks of
+ *                                              H^(0) + H^(1) + 1/2 [Htilde(1), A(1)]
+ *   "Hbar1_3" [2na][2na], "Hbar2_3" [2na]^4    all-active blocks of
+ *                                              1/2 [Htilde(1), A(2)] + 1/2 [Htilde(2), A(1)]
+ *                                              (the last dsrg_relaxed call)
  * Spin blocks that change the number of alpha electrons are zero (the library
  * does not store them and fills them in on the copy).  O1 and O2 are kept
  * only while one [P,P,H,H] tensor takes at most 1 GiB (stored blocks);

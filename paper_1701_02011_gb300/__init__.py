@@ -45,10 +45,18 @@ class dsrg_energies(ctypes.Structure):
                 ("e3", ctypes.c_double)]
 
 
+class dsrg_relaxed_energies(ctypes.Structure):
+    _fields_ = [("e2", ctypes.c_double), ("e3a", ctypes.c_double), ("e3b", ctypes.c_double),
+                ("e3", ctypes.c_double), ("e_relaxed2", ctypes.c_double), ("e_relaxed3", ctypes.c_double),
+                ("residual2", ctypes.c_double), ("residual3", ctypes.c_double), ("ndet", ctypes.c_longlong),
+                ("steps2", ctypes.c_int), ("steps3", ctypes.c_int)]
+
+
 EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_pt3_batch", "dsrg_free", "dsrg_last_error",
            "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
            "dsrg_profile_step",
-           "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc", "dsrg_split_gemm", "dsrg_cholesky")
+           "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc", "dsrg_split_gemm", "dsrg_cholesky",
+           "dsrg_relaxed")
 
 _lib = None
 
@@ -68,6 +76,8 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
     for f in ("dsrg_pt2", "dsrg_pt3"):
         getattr(L, f).argtypes = [ctypes.c_void_p, ctypes.POINTER(dsrg_energies)]
         getattr(L, f).restype = ctypes.c_int
+    L.dsrg_relaxed.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dsrg_relaxed_energies)]
+    L.dsrg_relaxed.restype = ctypes.c_int
     L.dsrg_pt3_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(dsrg_energies)]
     L.dsrg_pt3_batch.restype = ctypes.c_int
     L.dsrg_free.argtypes = [ctypes.c_void_p]
@@ -185,6 +195,14 @@ def dsrg_pt3(h) -> dict:
     return _energies(load_library().dsrg_pt3, h)
 
 
+def dsrg_relaxed(h, n_alpha: int, n_beta: int) -> dict:
+    """Unrelaxed components and the one-step relaxed DSRG-MRPT2/PT3 energies
+    (relative to E0) over the determinants with n_alpha, n_beta active electrons."""
+    out = dsrg_relaxed_energies()
+    _check(load_library().dsrg_relaxed(h, int(n_alpha), int(n_beta), ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in dsrg_relaxed_energies._fields_}
+
+
 def dsrg_pt3_batch(handles) -> list:
     """PT3 energies of several handles at once (graph-captured after the first
     call per handle); handles are raw handles or Dsrg objects."""
@@ -258,6 +276,10 @@ def tensor_shape(name: str, nc: int, na: int, nv: int):
         return (p, h)
     if name in ("T2", "T2b", "O2"):
         return (p, p, h, h)
+    if name in ("Hbar1_2", "Hbar1_3"):
+        return (2 * na, 2 * na)
+    if name in ("Hbar2_2", "Hbar2_3"):
+        return (2 * na,) * 4
     raise KeyError(name)
 
 
@@ -340,6 +362,9 @@ class Dsrg:
 
     def pt3(self):
         return dsrg_pt3(self.h)
+
+    def relaxed(self, n_alpha: int, n_beta: int):
+        return dsrg_relaxed(self.h, n_alpha, n_beta)
 
     def fetch(self, name):
         return dsrg_fetch(self.h, name, *self.sizes)

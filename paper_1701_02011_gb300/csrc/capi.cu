@@ -341,6 +341,44 @@ int dsrg_pt3_batch(dsrg_handle* const* hs, int n, dsrg_energies* out) {
   return DSRG_OK;
 }
 
+int dsrg_relaxed(dsrg_handle* hd, int n_alpha, int n_beta, dsrg_relaxed_energies* out) {
+  g_last_error.clear();
+  if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
+  if (!out) return fail(DSRG_ERR_ARG, "out is required");
+  dsrg::Handle& h = *hd->h;
+  if (n_alpha < 0 || n_beta < 0 || n_alpha > h.na || n_beta > h.na)
+    return fail(DSRG_ERR_ARG, "n_alpha and n_beta must lie in [0, na]");
+  const long long ndet = dsrg::relax_ndet(h.na, n_alpha, n_beta);
+  if (ndet > 20000) return fail(DSRG_ERR_ARG, "more than 20000 determinants");
+  struct Flag {
+    dsrg::Handle& h;
+    ~Flag() { h.relax = false; }
+  } flag{h};
+  try {
+    h.relax = true;
+    dsrg_energies e{};
+    eager_energy(h, true, &e);
+    h.relax = false;
+    const dsrg::RelaxResult r2 = dsrg::relaxed_ci(h, 2, n_alpha, n_beta);
+    const dsrg::RelaxResult r3 = dsrg::relaxed_ci(h, 3, n_alpha, n_beta);
+    check_status(h);
+    out->e2 = e.e2;
+    out->e3a = e.e3a;
+    out->e3b = e.e3b;
+    out->e3 = e.e3;
+    out->e_relaxed2 = r2.e;
+    out->e_relaxed3 = r3.e;
+    out->residual2 = r2.residual;
+    out->residual3 = r3.residual;
+    out->ndet = ndet;
+    out->steps2 = r2.steps;
+    out->steps3 = r3.steps;
+  } catch (const std::exception& e) {
+    return fail(classify(e), e.what());
+  }
+  return DSRG_OK;
+}
+
 int dsrg_pt2(dsrg_handle* hd, dsrg_energies* out) { return run(hd, false, out); }
 int dsrg_pt3(dsrg_handle* hd, dsrg_energies* out) { return run(hd, true, out); }
 
@@ -418,6 +456,10 @@ int dsrg_fetch(const dsrg_handle* hd, const char* name, double* dst, long long c
   else if (!strcmp(name, "T2b")) t = &h.T2b;
   else if (!strcmp(name, "O1")) t = &h.O1;
   else if (!strcmp(name, "O2")) t = &h.O2;
+  else if (!strcmp(name, "Hbar1_2")) t = &h.rx1_2;
+  else if (!strcmp(name, "Hbar2_2")) t = &h.rx2_2;
+  else if (!strcmp(name, "Hbar1_3")) t = &h.rx1_3;
+  else if (!strcmp(name, "Hbar2_3")) t = &h.rx2_3;
   else return fail(DSRG_ERR_ARG, std::string("unknown tensor ") + name);
   if (!t->v.p) return fail(DSRG_ERR_STATE, std::string(name) + " has not been computed");
   // the dense spin-major layout: every spin block, blocks not stored are zero

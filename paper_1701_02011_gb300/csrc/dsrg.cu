@@ -689,7 +689,7 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   // own boxes) so that no work is spent where a piece vanishes.
   {
     ProfTag ring_tag(ws, "ring");
-    Iv xi = exc ? P : H, wi = exc ? H : P;
+    Iv xi = isect(exc ? P : H, C2.v.iv[0]), wi = isect(exc ? H : P, C2.v.iv[3]);
     Iv want[4] = {xi, H, P, wi};
     // y and u must land in C2's slots as well as in T2's
     Iv kiv[4] = {xi, isect(P, C2.v.iv[1]), isect(H, C2.v.iv[2]), wi};
@@ -834,6 +834,44 @@ void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const 
 }
 
 // E(2), E3a, E3b from their result slots, into the last three slots
+// ---------------------------------------------------------------------------
+// all-active blocks for the relaxed energies (App. A)
+// ---------------------------------------------------------------------------
+// H^(0) + H^(1) on [A, A] and [A, A, A, A]: the semicanonical Fock diagonal
+// and V (the off-diagonal Fock f^(1) has no all-active block)
+static void relax_bare(Handle& h, const Sym2& V) {
+  h.rx1_2 = mk_dense(h, {h.A, h.A});
+  h.rx2_2 = mk_dense(h, {h.A, h.A, h.A, h.A});
+  h.rx1_3 = mk_dense(h, {h.A, h.A});
+  h.rx2_3 = mk_dense(h, {h.A, h.A, h.A, h.A});
+  int r = h.ws.begin(K_AMP, 0.0, 0.0);
+  launch_active_diagonal(h.nc, h.na, h.eps, h.rx1_2.v.p, h.ws.stream);
+  h.ws.end(r);
+  fetch_x2(h.ws, 1.0, Op2{&V, 1.0, nullptr, 0.0}, h.rx2_2);
+}
+
+// [X, A]_act = C + C^+ with C = [X, T] on the all-active block, accumulated
+// into acc1, acc2
+static void relax_commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2,
+                             const Op1Pieces* pc, Tensor& acc1, Tensor& acc2) {
+  ProfTag tag_(h.ws, "relax-active");
+  Tensor C1 = mk(h, {h.A, h.A});
+  Tensor C2 = mk(h, {h.A, h.A, h.A, h.A});
+  commutator(h, X1, X2, T1, T2, C1, C2, false, pc);
+  axpy(h.ws, 1.0, C1.v, "uv", acc1, "uv");
+  axpy(h.ws, 1.0, C1.v, "uv", acc1, "vu");
+  axpy(h.ws, 1.0, C2.v, "uvxy", acc2, "uvxy");
+  axpy(h.ws, 1.0, C2.v, "uvxy", acc2, "xyuv");
+}
+
+// zero the all-active (internal) block of an excitation-block tensor
+static void zero_internal(Handle& h, Tensor& X) {
+  Iv want[4] = {h.A, h.A, h.A, h.A};
+  View in = X.v.sub(want);
+  const char* l = X.v.rank == 2 ? "ab" : "abcd";
+  axpy(h.ws, -1.0, in, l, X, l);
+}
+
 static void sum_components(Handle& h) {
   Workspace& ws = h.ws;
   if (ws.nresults > ws.cap_results - 3) throw std::runtime_error("out of result slots");
@@ -870,6 +908,8 @@ void issue_energy(Handle& h, bool pt3) {
   // the [P,P,P,H] class is read only by terms evaluated in density-fitted
   // form (df_x2t1, df_vd_onebody) and by small slabs of it: not stored
   build_v(h, pt3 ? 0x0fu : (1u << 2), V, pt3);
+  const bool rx = h.relax && pt3 && h.na > 0;
+  if (rx) relax_bare(h, V);
   ws.tag = "E2";
   Tensor Xs1 = build_x1(h, 2.0, &W1, 1.0);
   Op2 Xs2{&V, 2.0, &W2, 1.0};
@@ -893,11 +933,17 @@ void issue_energy(Handle& h, bool pt3) {
     Tensor X1 = build_x1(h, 1.0, &W1, 0.5);
     Op1Pieces pc = op1_pieces(h, 1.0, &W1, 0.5);
     commutator_A(h, X1, Op2{&V, 1.0, &W2, 0.5}, t1, t2, O1, O2, true, &pc);
+    if (rx) relax_commutator(h, X1, Op2{&V, 1.0, &W2, 0.5}, t1, t2, &pc, h.rx1_2, h.rx2_2);
   }
   // second-order amplitudes (Eqs. T1_2nd, T2_2nd) and [H(0), A(2)]
   ws.tag = "second-order";
   Tensor U1, U2, V1, V2;
   amplitudes(h, &O1, O2, U1, U2, V1, V2);
+  if (rx) {  // 1/2 [Htilde^(1), A^(2)] = [H^(1) + W/2, A^(2)]
+    Tensor X1 = build_x1(h, 1.0, &W1, 0.5);
+    Op1Pieces pc = op1_pieces(h, 1.0, &W1, 0.5);
+    relax_commutator(h, X1, Op2{&V, 1.0, &W2, 0.5}, U1, U2, &pc, h.rx1_3, h.rx2_3);
+  }
   // Htilde(2)_{1,2} excitation blocks = [H0, A(2)] + O - [W, A(1)] / 6,
   // accumulated in place of [H0, A(2)] (not needed otherwise); O is kept for
   // dsrg_fetch only while a [P,P,H,H] tensor is small
@@ -934,6 +980,18 @@ void issue_energy(Handle& h, bool pt3) {
   h.res[3] = ws.nresults;
   scalar(h, Zx1, Op2{nullptr, 0.0, &Z2, 1.0}, t1, t2);
   h.res[4] = ws.nresults;
+  if (rx) {
+    // 1/2 [Htilde^(2), A^(1)]: only the excitation blocks of Htilde^(2) and
+    // their Hermitian images reach the all-active block, and not their own
+    // all-active part (it meets only internal amplitudes, which vanish); it is
+    // removed so that the W-form operator does not count it twice
+    Zx1.release();
+    zero_internal(h, Z1);
+    zero_internal(h, Z2);
+    Tensor X1 = build_x1(h, 0.0, &Z1, 0.5);
+    Op1Pieces pc = op1_pieces(h, 0.0, &Z1, 0.5);
+    relax_commutator(h, X1, Op2{nullptr, 0.0, &Z2, 0.5}, t1, t2, &pc, h.rx1_3, h.rx2_3);
+  }
   h.T1b = std::move(U1);
   h.T2b = std::move(U2);
   sum_components(h);

@@ -24,6 +24,14 @@ struct Handle {
   Tensor gam_dI, eta_dI;
   // intermediates of the last evaluation
   Tensor T1, T2, T1b, T2b, O1, O2;
+  // relaxed energies (Eq. E_relaxed): with `relax` set, an energy also
+  // accumulates the all-active blocks of the summed transformed Hamiltonian
+  // relative to E0, dense spin-major over [A, A] and [A, A, A, A]:
+  // second order (H^(0) + H^(1) + 1/2 [Htilde^(1), A^(1)]) in rx1_2, rx2_2,
+  // the third-order terms (1/2 [Htilde^(1), A^(2)] + 1/2 [Htilde^(2), A^(1)])
+  // in rx1_3, rx2_3
+  bool relax = false;
+  Tensor rx1_2, rx2_2, rx1_3, rx2_3;
   long long launches = 0;
   long long d2h_bytes = 0;
   // result-slot boundaries of the last issued energy: E(2) [res0, res1),
@@ -70,5 +78,17 @@ void scalar(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const 
 void run_energy(Handle& h, bool pt3, double* e2, double* e3a, double* e3b);
 void issue_energy(Handle& h, bool pt3);
 void finish_energy(Handle& h, double* e2, double* e3a, double* e3b);
+
+// lowest eigenvalue of the order-2 or order-3 relaxed CASCI problem over the
+// determinants with n_alpha, n_beta active electrons, from the blocks the
+// last energy (run with relax set) accumulated
+struct RelaxResult {
+  double e = 0.0, residual = 0.0;
+  int steps = 0;
+};
+long long relax_ndet(int na, int n_alpha, int n_beta);
+// h1[u][u] += eps[nc + u] on both spins of a dense [A, A] block
+void launch_active_diagonal(int nc, int na, const double* eps, double* h1, cudaStream_t st);
+RelaxResult relaxed_ci(Handle& h, int order, int n_alpha, int n_beta);
 
 }  // namespace dsrg
