@@ -362,6 +362,8 @@ int dsrg_relaxed(dsrg_handle* hd, int n_alpha, int n_beta, dsrg_relaxed_energies
     const dsrg::RelaxResult r2 = dsrg::relaxed_ci(h, 2, n_alpha, n_beta);
     const dsrg::RelaxResult r3 = dsrg::relaxed_ci(h, 3, n_alpha, n_beta);
     check_status(h);
+    h.launches = h.ws.launches;
+    h.ws.prof_collect();
     out->e2 = e.e2;
     out->e3a = e.e3a;
     out->e3b = e.e3b;

@@ -125,6 +125,7 @@ const char* kernel_name(int id) {
     case K_DOT: return "k_dot";
     case K_AMP: return "k_amp";
     case K_OZAKI_PACK: return "k_ozaki_pack";
+    case K_CI_MATVEC: return "k_matvec";
     case K_OZAKI_MMA: return "k_ozaki_mma";
     default: return "?";
   }
@@ -271,11 +272,14 @@ bool split_faster(Workspace& ws, const GemmArgs& g) {
 // outputs use 32-column tiles, short ones split k over CTAs.  With tuning,
 // products of 5e6 .. 5e7 flops, and products whose shorter output side is
 // at most 32 (where packing the long operand can cost more than the FP64
-// work) up to 1e11 flops, take whichever path was faster on their shape.
+// work) up to 1e11 flops, take whichever path was faster on their shape;
+// so do products of at least 5e7 flops with k below 32 (contractions over
+// the active orbitals only), which stay on the FP64 units untuned.
 bool split_route(Workspace& ws, const GemmArgs& g) {
-  if (!(ws.slices > 0 && g.nbatch == 1 && g.K >= 32 && ozaki_supported(g))) return false;
+  if (!(ws.slices > 0 && g.nbatch == 1 && ozaki_supported(g))) return false;
   const double fl = 2.0 * (double)g.M * (double)g.N * (double)g.K;
   const bool timed = ws.tune && g.A && g.B && g.C;
+  if (g.K < 32) return timed && g.K >= 8 && fl >= 5e7 && split_faster(ws, g);
   const long long nmin = g.M < g.N ? g.M : g.N;
   if (timed && nmin <= 32 && fl >= 5e6 && fl < 1e11) return split_faster(ws, g);
   if (fl >= 5e7) return true;

@@ -62,7 +62,10 @@ class Workspace;
 
 // Kernels whose launches can be timed one by one (opt-in) with CUDA events on
 // the launching stream.
-enum KernelId { K_GEMM = 0, K_LADDER_BUILD, K_LADDER_CONTRACT, K_AXPY, K_DOT, K_AMP, K_OZAKI_PACK, K_OZAKI_MMA, K_NKERNELS };
+enum KernelId {
+  K_GEMM = 0, K_LADDER_BUILD, K_LADDER_CONTRACT, K_AXPY, K_DOT, K_AMP, K_OZAKI_PACK, K_OZAKI_MMA, K_CI_MATVEC,
+  K_NKERNELS
+};
 const char* kernel_name(int id);
 
 struct Tensor {

@@ -412,9 +412,12 @@ RelaxResult relaxed_ci(Handle& h, int order, int n_alpha, int n_beta) {
     k_dots<<<1, RX_T, 0, st>>>(ndet, x.p, x.p, nrm, nullptr);
     k_lz_start<<<gn, 256, 0, st>>>(ndet, x.p, nrm, V.p, lst);
     ws.launches += 2;
+    const double mv_bytes = 8.0 * (double)ndet * (double)ndet + 16.0 * (double)ndet;
     for (int j = 0; j < mmax; ++j) {
       const double* vj = V.p + (long long)j * ndet;
+      const int rec = ws.begin(K_CI_MATVEC, 2.0 * (double)ndet * (double)ndet, mv_bytes);
       k_matvec<<<gw, 256, 0, st>>>(ndet, H.p, vj, w.p, lst);
+      ws.end(rec);
       k_dots<<<j + 1, RX_T, 0, st>>>(ndet, V.p, w.p, coef, lst);
       k_subtract<<<gn, 256, 0, st>>>(ndet, j + 1, V.p, coef, w.p, lst);
       k_dots<<<j + 1, RX_T, 0, st>>>(ndet, V.p, w.p, coef2, lst);
@@ -422,7 +425,7 @@ RelaxResult relaxed_ci(Handle& h, int order, int n_alpha, int n_beta) {
       k_dots<<<1, RX_T, 0, st>>>(ndet, w.p, w.p, nrm, lst);
       k_lz_next<<<1, 1, 0, st>>>(j, mmax, coef, nrm, alpha, beta, lst);
       k_lz_scale<<<gn, 256, 0, st>>>(ndet, j, w.p, beta, V.p, lst);
-      ws.launches += 8;
+      ws.launches += 7;
     }
     check_cuda(cudaGetLastError(), "lanczos launch");
     k_lz_tridiag<<<1, 1, 0, st>>>(alpha, beta, lst, y, work.p);
