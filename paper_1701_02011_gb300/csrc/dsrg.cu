@@ -611,16 +611,21 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     contract_x2(ws, -0.5, X2, "pqrs", D2.v, "rsqj", C1, "pj");
   }
   {
-    Tensor Ehh = dress(h, dress(h, T2, 2, g), 3, g);
-    contract_x2(ws, 0.5, X2, "pqrs", Ehh.v, "abpq", C2, "abrs");  // hole ladder
-    Tensor D3 = dress(h, std::move(Ehh), 0, e);
-    contract_x2(ws, -0.5, X2, "pqrs", D3.v, "rbpq", C1, "bs");
-  }
-  {
+    // hole ladder 1/2 X2 (gamma gamma T2 - eta eta T2) as one product: the
+    // eta-dressed tensor lives on the active box inside the gamma-dressed one
+    // (eta vanishes on core); then the one-body pair (eta-dressed Ehh plus
+    // gamma-dressed Nhh) likewise
     Tensor Nhh = dress(h, dress(h, T2, 2, e), 3, e);
-    contract_x2(ws, -0.5, X2, "pqrs", Nhh.v, "abpq", C2, "abrs");  // hole ladder
-    Tensor D4 = dress(h, std::move(Nhh), 0, g);
-    contract_x2(ws, -0.5, X2, "pqrs", D4.v, "rbpq", C1, "bs");
+    Tensor D4 = dress(h, Nhh, 0, g);
+    Tensor Ehh = dress(h, dress(h, T2, 2, g), 3, g);
+    axpy(ws, -1.0, Nhh.v, "abij", Ehh, "abij");
+    contract_x2(ws, 0.5, X2, "pqrs", Ehh.v, "abpq", C2, "abrs");
+    axpy(ws, 1.0, Nhh.v, "abij", Ehh, "abij");
+    Nhh.release();
+    Tensor D3 = dress(h, std::move(Ehh), 0, e);
+    axpy(ws, 1.0, D4.v, "abij", D3, "abij");
+    D4.release();
+    contract_x2(ws, -0.5, X2, "pqrs", D3.v, "rbpq", C1, "bs");
   }
   // [X2, T2] one-body with a two-body cumulant
   ws.tag = "c-cumulant";
@@ -694,13 +699,15 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     // y and u must land in C2's slots as well as in T2's
     Iv kiv[4] = {xi, isect(P, C2.v.iv[1]), isect(H, C2.v.iv[2]), wi};
     Tensor K = make_tensor(ws, 4, kiv, true);
+    // (Xbar - Xtilde) as one operand: Xtilde (eta on the hole slot, gamma on
+    // the particle slot) lives on the active box inside Xbar's
     auto ring_piece = [&](const Tensor& Xs) {
+      Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
       {
-        Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
-        contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+        Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
+        axpy(ws, -1.0, Xt.v, "xiaw", Xb, "xiaw");
       }
-      Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
-      contract(ws, -1.0, Xt.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+      contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
     };
     if (X2.V && X2.cv != 0.0) {
       Tensor Xs = make_tensor(ws, 4, want, true);
