@@ -40,7 +40,7 @@ WORKLOAD = "cas88_c30_v300_q1200"
 # digit slices of the split path per workload: enough for 1e-6 Eh on energies
 # of up to 1e4 (6), 1e5 (7) and 1e7 Eh (8)
 SLICES = {"cas66_c10_v100_q400": 6, "cas88_c30_v300_q1200": 7, "cas44_c40_v500_q1800": 8, "scan32": 7,
-          "cas1616_c10_v100_q400": 7}
+          "cas1616_c10_v100_q400": 6}
 # FP64 runs on the SM's FP64 FMA units (no tcgen05 FP64 kind): 152 SMs x
 # 2 FP64 FMA per clock per SM x 2 flop x 2.070 GHz maximum SM clock.
 FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12

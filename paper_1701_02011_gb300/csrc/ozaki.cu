@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const PackPass pp) {
 // |V| <= 2^(7S - 1) (|x| < 2^e, e the row / column exponent), written as
 // V = sum_t d_t 128^(S - t) with |d_t| <= 64, so x = 2^(e + 1) sum_t d_t 2^(-7t);
 // the digits are extracted from the lowest up with balanced remainders and
-// stored as bf16 (magnitudes 0..64 from a shared table, sign bit set)
+// stored as bf16 (exact: |d| <= 64)
 template <int S>
 __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
   const int o = blockIdx.y;
@@ -752,9 +752,6 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
   const int kfast = pp.kfast[o];
   const FastDiv fQ = pp.fQ[o], fR = pp.fR[o];
   const unsigned W = pp.W[o];
-  __shared__ uint32_t bf[65];
-  if (threadIdx.x < 65) bf[threadIdx.x] = __float_as_uint((float)threadIdx.x) >> 16;  // exact for 0..64
-  __syncthreads();
   const long long tile_elems = (long long)p.TR * OZ_BK;
   constexpr int F = 7 * S - 1;
   const unsigned stride = gridDim.x * PACK_T;
@@ -786,13 +783,26 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
         else v = (m >> (-sh_)) + ((m >> (-sh_ - 1)) & 1ULL);  // to nearest, ties away from zero
         V = bits < 0 ? -(long long)v : (long long)v;
       }
+      // V = hi 2^28 + lo, 0 <= lo < 2^28: a digit depends only on the running
+      // value mod 128, so the (at most) four lowest digits come from lo in
+      // 32-bit arithmetic (lo - d >= 0 stays exact), then the carry joins the
+      // upper part for the rest
+      constexpr int NL = S - 1 < 4 ? S - 1 : 4;
+      int lo = (int)(V & 0xFFFFFFFLL), hi = (int)(V >> 28);
 #pragma unroll
-      for (int t = S; t >= 2; --t) {
-        const long long d = ((V + 64) & 127) - 64;
-        dg[t - 1][j] = (int)d;
-        V = (V - d) >> 7;
+      for (int k = 0; k < NL; ++k) {
+        const int d = ((lo + 64) & 127) - 64;
+        dg[S - 1 - k][j] = d;
+        lo = (lo - d) >> 7;
       }
-      dg[0][j] = (int)V;  // |V| <= 64 here
+      hi = lo + hi * (1 << (28 - 7 * NL));
+#pragma unroll
+      for (int k = NL; k < S - 1; ++k) {
+        const int d = ((hi + 64) & 127) - 64;
+        dg[S - 1 - k][j] = d;
+        hi = (hi - d) >> 7;
+      }
+      dg[0][j] = hi;  // |hi| <= 64 here
     }
     const unsigned tr = r / p.TR, rr = r - tr * p.TR;  // TR is 32, 64 or 128
     const int tk = (int)(q >> 1), chunk = (int)(q & 1);   // two 8-element chunks per 16-k row
@@ -802,14 +812,9 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
       uint32_t w[4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        uint32_t pair = 0;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int d = dg[t - 1][2 * h + u];
-          const uint32_t mag = min((uint32_t)(d < 0 ? -d : d), 64u);  // |d| <= 64 by construction
-          pair |= (bf[mag] | (d < 0 ? 0x8000u : 0u)) << (16 * u);
-        }
-        w[h] = pair;
+        // |d| <= 64: exact in float and in bf16, so the conversion is exact
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn((float)dg[t - 1][2 * h], (float)dg[t - 1][2 * h + 1]);
+        w[h] = *reinterpret_cast<const uint32_t*>(&b2);
       }
       const long long tile = ((long long)(t - 1) * p.T + tr) * p.KT + tk;
       *reinterpret_cast<uint4*>(dst + tile * tile_elems + within) = make_uint4(w[0], w[1], w[2], w[3]);
