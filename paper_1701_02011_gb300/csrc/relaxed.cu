@@ -253,6 +253,10 @@ __global__ void k_lz_tridiag(const double* __restrict__ a, const double* __restr
     double nrm = 0.0;
     for (int i = 0; i < k; ++i) nrm += z[i] * z[i];
     nrm = sqrt(nrm);
+    if (!(nrm > 0.0) || !isfinite(nrm)) {  // degenerate scale (e.g. a zero matrix): first basis vector
+      for (int i = 0; i < k; ++i) y[i] = i == 0 ? 1.0 : 0.0;
+      break;
+    }
     for (int i = 0; i < k; ++i) y[i] = z[i] / nrm;
   }
   st->lambda = lam;
