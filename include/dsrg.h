@@ -161,6 +161,36 @@ typedef struct {
  */
 int dsrg_relaxed(dsrg_handle *h, int n_alpha, int n_beta, dsrg_relaxed_energies *out);
 
+typedef struct {
+  int iterations;                 /* Jacobi steps taken                          */
+  int converged;                  /* 1: max |residual| <= tol x max |V[e,f,u,v]| */
+  double max_residual;            /* largest |residual| of the returned amplitudes */
+  double max_source;              /* largest |V[e,f,u,v]|                        */
+  double min_shifted_denominator; /* smallest |Ds| over e, f and u != v          */
+  long long pairs_not_converged;  /* virtual spin-orbital pairs (e, f) whose
+                                     largest |residual| exceeds the tolerance    */
+  long long small_denominators;   /* elements with |Ds| < 1e-2                   */
+} dsrg_dyall_result;
+
+/*
+ * First-order aavv amplitudes with Dyall's zeroth-order Hamiltonian (paper
+ * App. B, Eq. t2_aavv) at s -> infinity: for virtual spin orbitals e, f and
+ * active u, v,
+ *   0 = V[e,f,u,v] - D t[e,f,u,v] - 1/2 sum_xy Va[x,y,u,v] t[e,f,x,y]
+ *                                 + sum_xyz Va[x,y,u,v] t[e,f,x,z] gamma[y,z]
+ * (D = eps_u + eps_v - eps_e - eps_f, Va the all-active block of V).  Solved
+ * by Jacobi iteration preconditioned by the shifted denominator Ds, the exact
+ * diagonal of the system (D + Va[u,v,u,v] - sum_y (Va[u,y,u,v] gamma[y,v] -
+ * Va[v,y,u,v] gamma[y,u])), until max |residual| <= tol x max |V| or max_iter
+ * steps, or until the residual grows past 1e8 x max |V| (small shifted
+ * denominators: the intruders App. B discusses).  No counterpart energy is
+ * defined by the paper; the amplitudes are fetched as "Taavv".  The split
+ * path runs the coupling product on the tensor cores.  Synchronises the
+ * handle's stream.  Errors: DSRG_ERR_ARG (tol <= 0, max_iter < 1, out NULL),
+ * DSRG_ERR_STATE (NULL handle), otherwise as dsrg_pt3.
+ */
+int dsrg_dyall_aavv(dsrg_handle *h, double tol, int max_iter, dsrg_dyall_result *out);
+
 /*
  * PT3 energies of n independent instances (the points of a potential-energy
  * scan, any sizes), all in flight at once: handle i's energy runs on its own
@@ -320,6 +350,8 @@ int dsrg_split_gemm(long long M, long long N, long long K, const double *A, long
  *   "Hbar1_3" [2na][2na], "Hbar2_3" [2na]^4    all-active blocks of
  *                                              1/2 [Htilde(1), A(2)] + 1/2 [Htilde(2), A(1)]
  *                                              (the last dsrg_relaxed call)
+ *   "Taavv" [2nv][2nv][2na][2na]               aavv amplitudes of the last
+ *                                              dsrg_dyall_aavv call
  * Spin blocks that change the number of alpha electrons are zero (the library
  * does not store them and fills them in on the copy).  O1 and O2 are kept
  * only while one [P,P,H,H] tensor takes at most 1 GiB (stored blocks);

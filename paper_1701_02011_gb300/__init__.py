@@ -52,11 +52,17 @@ class dsrg_relaxed_energies(ctypes.Structure):
                 ("steps2", ctypes.c_int), ("steps3", ctypes.c_int)]
 
 
+class dsrg_dyall_result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("max_residual", ctypes.c_double),
+                ("max_source", ctypes.c_double), ("min_shifted_denominator", ctypes.c_double),
+                ("pairs_not_converged", ctypes.c_longlong), ("small_denominators", ctypes.c_longlong)]
+
+
 EXPORTS = ("dsrg_init", "dsrg_load", "dsrg_pt2", "dsrg_pt3", "dsrg_pt3_batch", "dsrg_free", "dsrg_last_error",
            "dsrg_last_launch_count", "dsrg_peak_bytes", "dsrg_fetch", "dsrg_profile", "dsrg_profile_stats",
            "dsrg_profile_step",
            "dsrg_last_d2h_bytes", "dsrg_df_ladder", "dsrg_df_ladder_noalloc", "dsrg_split_gemm", "dsrg_cholesky",
-           "dsrg_relaxed")
+           "dsrg_relaxed", "dsrg_dyall_aavv")
 
 _lib = None
 
@@ -78,6 +84,8 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         getattr(L, f).restype = ctypes.c_int
     L.dsrg_relaxed.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(dsrg_relaxed_energies)]
     L.dsrg_relaxed.restype = ctypes.c_int
+    L.dsrg_dyall_aavv.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.POINTER(dsrg_dyall_result)]
+    L.dsrg_dyall_aavv.restype = ctypes.c_int
     L.dsrg_pt3_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(dsrg_energies)]
     L.dsrg_pt3_batch.restype = ctypes.c_int
     L.dsrg_free.argtypes = [ctypes.c_void_p]
@@ -203,6 +211,14 @@ def dsrg_relaxed(h, n_alpha: int, n_beta: int) -> dict:
     return {k: getattr(out, k) for k, _ in dsrg_relaxed_energies._fields_}
 
 
+def dsrg_dyall_aavv(h, tol: float = 1e-10, max_iter: int = 200) -> dict:
+    """First-order aavv amplitudes with Dyall's H(0) at s -> infinity (App. B);
+    the amplitudes are fetched as "Taavv"."""
+    out = dsrg_dyall_result()
+    _check(load_library().dsrg_dyall_aavv(h, float(tol), int(max_iter), ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in dsrg_dyall_result._fields_}
+
+
 def dsrg_pt3_batch(handles) -> list:
     """PT3 energies of several handles at once (graph-captured after the first
     call per handle); handles are raw handles or Dsrg objects."""
@@ -280,6 +296,8 @@ def tensor_shape(name: str, nc: int, na: int, nv: int):
         return (2 * na, 2 * na)
     if name in ("Hbar2_2", "Hbar2_3"):
         return (2 * na,) * 4
+    if name == "Taavv":
+        return (2 * nv, 2 * nv, 2 * na, 2 * na)
     raise KeyError(name)
 
 
@@ -362,6 +380,9 @@ class Dsrg:
 
     def pt3(self):
         return dsrg_pt3(self.h)
+
+    def dyall_aavv(self, tol: float = 1e-10, max_iter: int = 200):
+        return dsrg_dyall_aavv(self.h, tol, max_iter)
 
     def relaxed(self, n_alpha: int, n_beta: int):
         return dsrg_relaxed(self.h, n_alpha, n_beta)

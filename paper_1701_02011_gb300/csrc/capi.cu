@@ -381,6 +381,30 @@ int dsrg_relaxed(dsrg_handle* hd, int n_alpha, int n_beta, dsrg_relaxed_energies
   return DSRG_OK;
 }
 
+int dsrg_dyall_aavv(dsrg_handle* hd, double tol, int max_iter, dsrg_dyall_result* out) {
+  g_last_error.clear();
+  if (!hd || !hd->h) return fail(DSRG_ERR_STATE, "NULL handle");
+  if (!out || !(tol > 0.0) || max_iter < 1) return fail(DSRG_ERR_ARG, "need out, tol > 0 and max_iter >= 1");
+  dsrg::Handle& h = *hd->h;
+  try {
+    h.drop_graph();
+    reset_status(h);
+    const dsrg::DyallResult r = dsrg::dyall_aavv(h, tol, max_iter);
+    check_status(h);
+    h.ws.prof_collect();
+    out->iterations = r.iterations;
+    out->converged = r.converged;
+    out->max_residual = r.max_residual;
+    out->max_source = r.max_source;
+    out->min_shifted_denominator = r.min_shifted_denominator;
+    out->pairs_not_converged = r.pairs_not_converged;
+    out->small_denominators = r.small_denominators;
+  } catch (const std::exception& e) {
+    return fail(classify(e), e.what());
+  }
+  return DSRG_OK;
+}
+
 int dsrg_pt2(dsrg_handle* hd, dsrg_energies* out) { return run(hd, false, out); }
 int dsrg_pt3(dsrg_handle* hd, dsrg_energies* out) { return run(hd, true, out); }
 
@@ -462,6 +486,7 @@ int dsrg_fetch(const dsrg_handle* hd, const char* name, double* dst, long long c
   else if (!strcmp(name, "Hbar2_2")) t = &h.rx2_2;
   else if (!strcmp(name, "Hbar1_3")) t = &h.rx1_3;
   else if (!strcmp(name, "Hbar2_3")) t = &h.rx2_3;
+  else if (!strcmp(name, "Taavv")) t = &h.t_aavv;
   else return fail(DSRG_ERR_ARG, std::string("unknown tensor ") + name);
   if (!t->v.p) return fail(DSRG_ERR_STATE, std::string(name) + " has not been computed");
   // the dense spin-major layout: every spin block, blocks not stored are zero

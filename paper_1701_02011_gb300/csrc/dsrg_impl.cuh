@@ -32,6 +32,8 @@ struct Handle {
   // in rx1_3, rx2_3
   bool relax = false;
   Tensor rx1_2, rx2_2, rx1_3, rx2_3;
+  // first-order aavv amplitudes of the Dyall-H(0) solve (dense, [V,V,A,A])
+  Tensor t_aavv;
   long long launches = 0;
   long long d2h_bytes = 0;
   // result-slot boundaries of the last issued energy: E(2) [res0, res1),
@@ -87,6 +89,14 @@ struct RelaxResult {
   int steps = 0;
 };
 long long relax_ndet(int na, int n_alpha, int n_beta);
+
+// first-order aavv amplitudes with Dyall's H(0) at s -> infinity (App. B)
+struct DyallResult {
+  int iterations = 0, converged = 0;
+  double max_residual = 0.0, max_source = 0.0, min_shifted_denominator = 0.0;
+  long long pairs_not_converged = 0, small_denominators = 0;
+};
+DyallResult dyall_aavv(Handle& h, double tol, int max_iter);
 // h1[u][u] += eps[nc + u] on both spins of a dense [A, A] block
 void launch_active_diagonal(int nc, int na, const double* eps, double* h1, cudaStream_t st);
 RelaxResult relaxed_ci(Handle& h, int order, int n_alpha, int n_beta);
