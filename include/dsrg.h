@@ -217,7 +217,8 @@ void dsrg_free(dsrg_handle *h);
 const char *dsrg_last_error(void);
 
 /* Number of this library's kernel launches issued by the last dsrg_pt2 /
- * dsrg_pt3 call on the handle (-1 on a NULL handle). */
+ * dsrg_pt3 / dsrg_relaxed / dsrg_dyall_aavv call on the handle (-1 on a
+ * NULL handle). */
 long long dsrg_last_launch_count(const dsrg_handle *h);
 
 /* Per-kernel timing.  dsrg_profile(h, 1) makes later dsrg_pt2/dsrg_pt3 calls

@@ -389,8 +389,10 @@ int dsrg_dyall_aavv(dsrg_handle* hd, double tol, int max_iter, dsrg_dyall_result
   try {
     h.drop_graph();
     reset_status(h);
+    h.ws.launches = 0;
     const dsrg::DyallResult r = dsrg::dyall_aavv(h, tol, max_iter);
     check_status(h);
+    h.launches = h.ws.launches;
     h.ws.prof_collect();
     out->iterations = r.iterations;
     out->converged = r.converged;

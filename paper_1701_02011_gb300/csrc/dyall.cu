@@ -68,28 +68,48 @@ struct DyDims {
   int nc, na, nv;
 };
 
-// R = V - D t + W (W = t K); t += R / Ds off the u = v diagonal; max |R|
+// R = V - D t + W (W = t K); t += R / Ds off the u = v diagonal; max |R|.
+// One CTA per virtual pair at a time (its m^2 elements are contiguous).  The
+// FP64 pipe is the narrow resource here, so per active pair dd = eps_u +
+// eps_v and ds = dd + diag come precomputed (pd[uv], pd[m2 + uv]) and the
+// preconditioner's reciprocal is taken in FP32: it scales the step only,
+// the residual that decides convergence stays FP64.
 __global__ void __launch_bounds__(DY_T) k_dy_update(const DyDims d, const double* __restrict__ eps,
                                                      const double* __restrict__ Vs, const double* __restrict__ W,
-                                                     const double* __restrict__ diag, double* __restrict__ t,
+                                                     const double* __restrict__ pd, double* __restrict__ t,
                                                      double* __restrict__ rmax, int update) {
-  const long long m2 = (long long)d.m * d.m, n = d.pairs * m2;
-  double mx = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / m2;
-    const int uv = (int)(i - p * m2), u = uv / d.m, v = uv % d.m;
-    if (u == v) continue;
-    const int e = (int)(p / (2 * d.nv)), f = (int)(p % (2 * d.nv));
-    const double D = eps_act(eps, d.nc, d.na, u) + eps_act(eps, d.nc, d.na, v) - eps_vir(eps, d.nc, d.na, d.nv, e) -
-                     eps_vir(eps, d.nc, d.na, d.nv, f);
-    const double ti = t[i];
-    const double R = Vs[i] - D * ti + W[i];
-    const double a = fabs(R);
-    mx = a == a ? fmax(mx, a) : INFINITY;  // a NaN residual counts as divergence
-    if (update) t[i] = ti + R / (D + diag[uv]);
+  const int m2 = d.m * d.m;
+  float mx = 0.0f;
+  for (long long p = blockIdx.x; p < d.pairs; p += gridDim.x) {
+    const int e = (int)(p / (2 * d.nv)), f = (int)(p - (long long)e * 2 * d.nv);
+    const double Ef = eps_vir(eps, d.nc, d.na, d.nv, e) + eps_vir(eps, d.nc, d.na, d.nv, f);
+    const long long base = p * m2;
+    for (int uv = threadIdx.x; uv < m2; uv += DY_T) {
+      const double dd = pd[uv];
+      if (dd != dd) continue;  // u = v: marked NaN
+      const long long i = base + uv;
+      const double ti = t[i];
+      const double R = fma(-(dd - Ef), ti, Vs[i] + W[i]);
+      const float a = fabsf((float)R);
+      mx = a == a ? fmaxf(mx, a) : INFINITY;  // a NaN residual counts as divergence
+      if (update) t[i] = fma(R, (double)(1.0f / (float)(pd[m2 + uv] - Ef)), ti);
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rmax, mx);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  // float max, widened: |R| is compared with the tolerance after the loop
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rmax, (double)mx);
+}
+
+// pd[uv] = eps_u + eps_v (NaN on u = v), pd[m2 + uv] = pd[uv] + diag[uv]
+__global__ void k_dy_pairs(int m, int nc, int na, const double* __restrict__ eps, const double* __restrict__ diag,
+                           double* __restrict__ pd) {
+  const int m2 = m * m;
+  for (int uv = blockIdx.x * blockDim.x + threadIdx.x; uv < m2; uv += gridDim.x * blockDim.x) {
+    const int u = uv / m, v = uv - u * m;
+    const double dd = u == v ? (double)NAN : eps_act(eps, nc, na, u) + eps_act(eps, nc, na, v);
+    pd[uv] = dd;
+    pd[m2 + uv] = dd + diag[uv];
+  }
 }
 
 // One warp per virtual pair: its largest |R| against thr (pairs above are
@@ -212,10 +232,11 @@ DyallResult dyall_aavv(Handle& h, double tol, int max_iter) {
   Iv aa[2] = {h.A, h.A};
   Tensor G = make_tensor(ws, 2, aa, true, true);
   axpy(ws, 1.0, h.gam.v.sub(aa), "ab", G, "ab");
-  DyBuf K(ws, (size_t)m2 * m2), diag(ws, (size_t)m2);
+  DyBuf K(ws, (size_t)m2 * m2), diag(ws, (size_t)m2), pd(ws, 2 * (size_t)m2);
   k_dy_coupling<<<dy_grid((long long)m2 * m2, DY_T), DY_T, 0, st>>>(m, Va.v.p, G.v.p, K.p, diag.p);
+  k_dy_pairs<<<dy_grid(m2, DY_T), DY_T, 0, st>>>(m, h.nc, h.na, h.eps, diag.p, pd.p);
   check_cuda(cudaGetLastError(), "dyall launch");
-  ws.launches += 1;
+  ws.launches += 2;
   // amplitudes, product buffer, reductions
   h.t_aavv = make_tensor(ws, 4, vvaa, true, true);
   double* t = h.t_aavv.v.p;
@@ -232,7 +253,7 @@ DyallResult dyall_aavv(Handle& h, double tol, int max_iter) {
       dy_product(h, t, K.p, W, pairs, m2);
       check_cuda(cudaMemsetAsync(scr, 0, sizeof(double), st), "cudaMemsetAsync (dyall)");
       const int rec = ws.begin(K_AMP, 0.0, 32.0 * (double)n);
-      k_dy_update<<<dy_grid(n, DY_T), DY_T, 0, st>>>(d, h.eps, Vs.v.p, W, diag.p, t, scr, 1);
+      k_dy_update<<<dy_grid(pairs * DY_T, DY_T), DY_T, 0, st>>>(d, h.eps, Vs.v.p, W, pd.p, t, scr, 1);
       ws.end(rec);
       check_cuda(cudaGetLastError(), "dyall launch");
       check_cuda(cudaMemcpyAsync(&r, scr, sizeof r, cudaMemcpyDeviceToHost, st), "copy residual");
@@ -248,7 +269,7 @@ DyallResult dyall_aavv(Handle& h, double tol, int max_iter) {
     DyStats* dst = reinterpret_cast<DyStats*>(scr + 2);
     check_cuda(cudaMemcpyAsync(dst, &init, sizeof init, cudaMemcpyHostToDevice, st), "copy stats");
     check_cuda(cudaMemsetAsync(scr, 0, sizeof(double), st), "cudaMemsetAsync (dyall)");
-    k_dy_update<<<dy_grid(n, DY_T), DY_T, 0, st>>>(d, h.eps, Vs.v.p, W, diag.p, t, scr, 0);
+    k_dy_update<<<dy_grid(pairs * DY_T, DY_T), DY_T, 0, st>>>(d, h.eps, Vs.v.p, W, pd.p, t, scr, 0);
     k_dy_stats<<<dy_grid(pairs * 32, DY_T), DY_T, 0, st>>>(d, h.eps, Vs.v.p, W, diag.p, t, tol * vmax, dst);
     check_cuda(cudaGetLastError(), "dyall launch");
     ws.launches += 3;
