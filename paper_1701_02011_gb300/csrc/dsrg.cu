@@ -681,11 +681,23 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
       if (!df) throw std::runtime_error("particle ladder of V needs the DF path");
       df_ladder(h, T2, C2, X2.cv);
     }
-    contract_x2(ws, 0.5, X2, "pqrs", T2.v, "rsij", C2, "pqij", true);
+    Tensor gT2 = dress(h, T2, 0, g);
+    if (X2.W && X2.cw != 0.0) {
+      // W's excitation block [P,P,H,H] meets both terms only on its [A,A]
+      // second pair: one product with (1/2 T2 - gamma T2) on [A,A,H,H];
+      // its Hermitian image takes each term on its own
+      Iv box[4] = {A, A, H, H};
+      Tensor Y = make_tensor(ws, 4, box, true);
+      axpy(ws, 0.5, T2.v.sub(box), "rsij", Y, "rsij");
+      axpy(ws, -1.0, gT2.v.sub(box), "rsij", Y, "rsij");
+      contract(ws, X2.cw, w_place(*X2.W, 0), "pqrs", Y.v, "rsij", C2, "pqij");
+      contract(ws, 0.5 * X2.cw, w_place(*X2.W, 1), "pqrs", T2.v, "rsij", C2, "pqij");
+      contract(ws, -X2.cw, w_place(*X2.W, 1), "pqrb", gT2.v, "rbij", C2, "pqij");
+    }
+    if (X2.V && X2.cv != 0.0)
+      contract_x2(ws, -1.0, Op2{X2.V, X2.cv, nullptr, 0.0}, "pqrb", gT2.v, "rbij", C2, "pqij");
   } else {
     contract_x2(ws, 0.5, X2, "pqrs", T2.v, "rsij", C2, "pqij");
-  }
-  {
     Tensor gT2 = dress(h, T2, 0, g);
     contract_x2(ws, -1.0, X2, "pqrb", gT2.v, "rbij", C2, "pqij");
   }
