@@ -722,11 +722,13 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
       contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
     };
     if (X2.V && X2.cv != 0.0) {
+      // V covers the whole box: W's pieces are added into it, one product
       Tensor Xs = make_tensor(ws, 4, want, true);
       fetch_x2(ws, 1.0, Op2{X2.V, X2.cv, nullptr, 0.0}, Xs);
+      if (X2.W && X2.cw != 0.0)
+        for (int herm = 0; herm < 2; ++herm) axpy(ws, X2.cw, w_place(*X2.W, herm), "abcd", Xs, "abcd");
       ring_piece(Xs);
-    }
-    if (X2.W && X2.cw != 0.0) {
+    } else if (X2.W && X2.cw != 0.0) {
       for (int herm = 0; herm < 2; ++herm) {
         View wp = w_place(*X2.W, herm);
         Iv box[4];
