@@ -1,6 +1,7 @@
 // Device kernels of the DSRG-MRPT2/PT3 energy path (sm_103a), FP64.
 #include "kernels.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <stdexcept>
 
@@ -855,8 +856,34 @@ void launch_gemm(const GemmArgs& g, cudaStream_t st, int kind) {
 }
 
 namespace {
-// fills the fast divisors; true when every linear index fits 31 bits
-bool nd_prepare(NdArgs& g) {
+// Consecutive threads take consecutive linear indices, whose last dimension
+// runs fastest.  The dimensions are put in order of decreasing stride,
+// weighted wb for the second operand (the one written, for axpy), so that
+// the last one is the label with the smallest strides: stride 1 in both
+// operands when they share a contiguous label.  In the order the labels
+// were written, a permuted view (a transposed two-body class, the Hermitian
+// placement of W) put a stride of 10^3 - 10^5 elements on the fastest
+// dimension, and every 8-byte access then fetched its own DRAM sectors.
+// Only the order of the visits changes; the set of (A, B) element pairs is
+// the same.
+void nd_order(NdArgs& g, long long wb) {
+  int ord[kMaxDims];
+  for (int d = 0; d < g.nd; ++d) ord[d] = d;
+  std::stable_sort(ord, ord + g.nd, [&](int x, int y) {
+    return g.sa[x] + wb * g.sb[x] > g.sa[y] + wb * g.sb[y];
+  });
+  const NdArgs h = g;
+  for (int d = 0; d < g.nd; ++d) {
+    g.e[d] = h.e[ord[d]];
+    g.sa[d] = h.sa[ord[d]];
+    g.sb[d] = h.sb[ord[d]];
+  }
+}
+
+// orders the dimensions and fills the fast divisors; true when every linear
+// index fits 31 bits
+bool nd_prepare(NdArgs& g, long long wb) {
+  nd_order(g, wb);
   if (g.total >= (1LL << 31)) return false;
   for (int d = 0; d < g.nd; ++d) g.fe[d] = make_fastdiv((unsigned)g.e[d]);
   return true;
@@ -866,7 +893,7 @@ bool nd_prepare(NdArgs& g) {
 void launch_axpy(const NdArgs& g0, double alpha, const double* A, double* C, cudaStream_t st) {
   if (g0.total <= 0) return;
   NdArgs g = g0;
-  if (nd_prepare(g)) k_axpy<true><<<grid_for(g.total, 256), 256, 0, st>>>(g, alpha, A, C);
+  if (nd_prepare(g, 2)) k_axpy<true><<<grid_for(g.total, 256), 256, 0, st>>>(g, alpha, A, C);
   else k_axpy<false><<<grid_for(g.total, 256), 256, 0, st>>>(g, alpha, A, C);
 }
 
@@ -875,7 +902,7 @@ void launch_axpy_blocks(const NdArgs& g0, double alpha, const AxpyBlocks& p, cud
   NdArgs g = g0;
   const int gx = grid_for(g.total, 256, (152 * 16 + p.n - 1) / p.n);
   const dim3 grid((unsigned)gx, (unsigned)p.n);
-  if (nd_prepare(g)) k_axpy_blocks<true><<<grid, 256, 0, st>>>(g, alpha, p);
+  if (nd_prepare(g, 2)) k_axpy_blocks<true><<<grid, 256, 0, st>>>(g, alpha, p);
   else k_axpy_blocks<false><<<grid, 256, 0, st>>>(g, alpha, p);
 }
 
@@ -887,7 +914,7 @@ void launch_dot_blocks(const NdArgs& g0, double alpha, const DotBlocks& p, doubl
   if (cap < 1) throw std::runtime_error("dot: scratch too small for the spin blocks");
   const int gx = grid_for(g.total > 0 ? g.total : 1, DOT_THREADS, cap);
   const dim3 grid((unsigned)gx, (unsigned)p.n);
-  if (nd_prepare(g)) k_dot_blocks<true><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
+  if (nd_prepare(g, 1)) k_dot_blocks<true><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
   else k_dot_blocks<false><<<grid, DOT_THREADS, 0, st>>>(g, p, scratch, ticket, alpha, out);
 }
 

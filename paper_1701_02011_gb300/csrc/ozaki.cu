@@ -742,7 +742,84 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_rowexp(const PackPass pp) {
 // |V| <= 2^(7S - 1) (|x| < 2^e, e the row / column exponent), written as
 // V = sum_t d_t 128^(S - t) with |d_t| <= 64, so x = 2^(e + 1) sum_t d_t 2^(-7t);
 // the digits are extracted from the lowest up with balanced remainders and
-// stored as bf16 (exact: |d| <= 64)
+// stored as bf16 (exact: |d| <= 64).  One call: group q of row r, S 16-byte
+// stores (one per slice tile).
+template <int S>
+__device__ __forceinline__ void digits_item(const OzPack& p, const unsigned* eu, __nv_bfloat16* dst, unsigned r,
+                                            unsigned q) {
+  const long long tile_elems = (long long)p.TR * OZ_BK;
+  constexpr int F = 7 * S - 1;
+  long long x[8];
+  pack_load8(p, r, q, x);
+  const int e = r < (unsigned long long)p.R ? (int)eu[r] - (int)OZ_EBIAS : 0;
+  int dg[S][8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    long long V = 0;
+    const long long bits = x[j];
+    if ((bits << 1) != 0) {
+      const int be = (int)((bits >> 52) & 0x7FF);
+      unsigned long long m = (unsigned long long)(bits & ((1LL << 52) - 1));
+      int E;
+      if (be) {
+        m |= 1ULL << 52;
+        E = be - 1075;
+      } else {
+        E = -1074;
+      }
+      const int sh_ = E + F - e;  // |x| 2^(F - e) = m 2^sh < 2^F
+      unsigned long long v;
+      if (sh_ >= 0) v = sh_ < 12 ? (m << sh_) : 0;
+      else if (-sh_ >= 64) v = 0;
+      else v = (m >> (-sh_)) + ((m >> (-sh_ - 1)) & 1ULL);  // to nearest, ties away from zero
+      V = bits < 0 ? -(long long)v : (long long)v;
+    }
+    // V = hi 2^28 + lo, 0 <= lo < 2^28: a digit depends only on the running
+    // value mod 128, so the (at most) four lowest digits come from lo in
+    // 32-bit arithmetic (lo - d >= 0 stays exact), then the carry joins the
+    // upper part for the rest
+    constexpr int NL = S - 1 < 4 ? S - 1 : 4;
+    int lo = (int)(V & 0xFFFFFFFLL), hi = (int)(V >> 28);
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      const int d = ((lo + 64) & 127) - 64;
+      dg[S - 1 - k][j] = d;
+      lo = (lo - d) >> 7;
+    }
+    hi = lo + hi * (1 << (28 - 7 * NL));
+#pragma unroll
+    for (int k = NL; k < S - 1; ++k) {
+      const int d = ((hi + 64) & 127) - 64;
+      dg[S - 1 - k][j] = d;
+      hi = (hi - d) >> 7;
+    }
+    dg[0][j] = hi;  // |hi| <= 64 here
+  }
+  const unsigned tr = r / p.TR, rr = r - tr * p.TR;  // TR is 32, 64 or 128
+  const int tk = (int)(q >> 1), chunk = (int)(q & 1);   // two 8-element chunks per 16-k row
+  const long long within = (long long)rr * OZ_BK + ((chunk ^ ((rr >> 2) & 1)) << 3);
+#pragma unroll
+  for (int t = 1; t <= S; ++t) {
+    uint32_t w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      // |d| <= 64: exact in float and in bf16, so the conversion is exact
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn((float)dg[t - 1][2 * h], (float)dg[t - 1][2 * h + 1]);
+      w[h] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    const long long tile = ((long long)(t - 1) * p.T + tr) * p.KT + tk;
+    *reinterpret_cast<uint4*>(dst + tile * tile_elems + within) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// A 16-k row of a digit tile is 32 bytes, one DRAM sector, filled by its two
+// 8-element groups, and the two halves are written by neighbouring lanes:
+// along k the groups of a row are consecutive items anyway; along rows item
+// i takes row (i / 2) mod rows and group 2 ((i / 2) / rows) + i mod 2.  (With
+// rows alone along the lanes, the second half of every sector followed a
+// whole pass over the rows later, after the sector had left L2: each
+// half-sector write then cost a read-modify-write in DRAM, and the digit pass
+// moved 2-4x its bytes.)
 template <int S>
 __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
   const int o = blockIdx.y;
@@ -752,73 +829,17 @@ __global__ void __launch_bounds__(PACK_T) k_ozaki_digits(const PackPass pp) {
   const int kfast = pp.kfast[o];
   const FastDiv fQ = pp.fQ[o], fR = pp.fR[o];
   const unsigned W = pp.W[o];
-  const long long tile_elems = (long long)p.TR * OZ_BK;
-  constexpr int F = 7 * S - 1;
   const unsigned stride = gridDim.x * PACK_T;
   for (unsigned i = blockIdx.x * PACK_T + threadIdx.x; i < W; i += stride) {
     unsigned r, q;
-    pack_item(i, fQ, fR, kfast != 0, r, q);
-    long long x[8];
-    pack_load8(p, r, q, x);
-    const int e = r < (unsigned long long)p.R ? (int)eu[r] - (int)OZ_EBIAS : 0;
-    int dg[S][8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      long long V = 0;
-      const long long bits = x[j];
-      if ((bits << 1) != 0) {
-        const int be = (int)((bits >> 52) & 0x7FF);
-        unsigned long long m = (unsigned long long)(bits & ((1LL << 52) - 1));
-        int E;
-        if (be) {
-          m |= 1ULL << 52;
-          E = be - 1075;
-        } else {
-          E = -1074;
-        }
-        const int sh_ = E + F - e;  // |x| 2^(F - e) = m 2^sh < 2^F
-        unsigned long long v;
-        if (sh_ >= 0) v = sh_ < 12 ? (m << sh_) : 0;
-        else if (-sh_ >= 64) v = 0;
-        else v = (m >> (-sh_)) + ((m >> (-sh_ - 1)) & 1ULL);  // to nearest, ties away from zero
-        V = bits < 0 ? -(long long)v : (long long)v;
-      }
-      // V = hi 2^28 + lo, 0 <= lo < 2^28: a digit depends only on the running
-      // value mod 128, so the (at most) four lowest digits come from lo in
-      // 32-bit arithmetic (lo - d >= 0 stays exact), then the carry joins the
-      // upper part for the rest
-      constexpr int NL = S - 1 < 4 ? S - 1 : 4;
-      int lo = (int)(V & 0xFFFFFFFLL), hi = (int)(V >> 28);
-#pragma unroll
-      for (int k = 0; k < NL; ++k) {
-        const int d = ((lo + 64) & 127) - 64;
-        dg[S - 1 - k][j] = d;
-        lo = (lo - d) >> 7;
-      }
-      hi = lo + hi * (1 << (28 - 7 * NL));
-#pragma unroll
-      for (int k = NL; k < S - 1; ++k) {
-        const int d = ((hi + 64) & 127) - 64;
-        dg[S - 1 - k][j] = d;
-        hi = (hi - d) >> 7;
-      }
-      dg[0][j] = hi;  // |hi| <= 64 here
+    if (kfast) {
+      pack_item(i, fQ, fR, true, r, q);
+    } else {
+      const unsigned j = i >> 1, tk = fast_div(j, fR);
+      r = j - tk * fR.d;
+      q = 2u * tk + (i & 1u);
     }
-    const unsigned tr = r / p.TR, rr = r - tr * p.TR;  // TR is 32, 64 or 128
-    const int tk = (int)(q >> 1), chunk = (int)(q & 1);   // two 8-element chunks per 16-k row
-    const long long within = (long long)rr * OZ_BK + ((chunk ^ ((rr >> 2) & 1)) << 3);
-#pragma unroll
-    for (int t = 1; t <= S; ++t) {
-      uint32_t w[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        // |d| <= 64: exact in float and in bf16, so the conversion is exact
-        const __nv_bfloat162 b2 = __floats2bfloat162_rn((float)dg[t - 1][2 * h], (float)dg[t - 1][2 * h + 1]);
-        w[h] = *reinterpret_cast<const uint32_t*>(&b2);
-      }
-      const long long tile = ((long long)(t - 1) * p.T + tr) * p.KT + tk;
-      *reinterpret_cast<uint4*>(dst + tile * tile_elems + within) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
+    digits_item<S>(p, eu, dst, r, q);
   }
 }
 
