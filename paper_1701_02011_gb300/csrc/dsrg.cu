@@ -537,8 +537,12 @@ static Op1Pieces op1_pieces(Handle& h, double c_f, const Tensor* W1, double c_w)
   return o;
 }
 
-void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
-                Tensor& C2, bool df, const Op1Pieces* X1p) {
+// Blocks of [X, T] accumulated into each output pair (C1s[o], C2s[o]),
+// o < nout; the output pair's ranges select the blocks (C2 on [P,P,H,H]:
+// the excitation blocks).  The dressed copies of T2 depend on T only, so each
+// is formed once and serves every output pair before the next is formed.
+void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor* const* C1s,
+                Tensor* const* C2s, int nout, bool df, const Op1Pieces* X1p) {
   Workspace& ws = h.ws;
   ProfTag tag_(ws, "commutator");
   const Tensor& g = h.gam;
@@ -548,54 +552,60 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   const Iv& H = h.H;
   const Iv& P = h.P;
   const Iv& A = h.A;
-  const bool exc = (C2.v.iv[0].lo == P.lo && C2.v.iv[0].hi == P.hi);
-  // [X1, T1] one-body: X1 T1 - T1 X1
-  ws.tag = "c-x1";
-  contract(ws, 1.0, X1.v, "pr", T1.v, "rq", C1, "pq");
-  contract(ws, -1.0, T1.v, "pr", X1.v, "rq", C1, "pq");
-  // [X1, T2] one-body: (gamma X1 eta - eta X1 gamma)[i,a] T2[a,b,i,j]
-  {
-    Tensor M1 = mk(h, {G, G});
-    Tensor t1 = mk(h, {G, P});
-    contract(ws, 1.0, X1.v, "pq", e.v, "qa", t1, "pa");
-    contract(ws, 1.0, g.v, "ip", t1.v, "pa", M1, "ia");
-    Tensor t2 = mk(h, {G, H});
-    contract(ws, 1.0, X1.v, "pq", g.v, "qa", t2, "pa");
-    contract(ws, -1.0, e.v, "ip", t2.v, "pa", M1, "ia");
-    contract(ws, 1.0, M1.v, "ia", T2.v, "abij", C1, "bj");
-  }
-  // [X1, T2] two-body, piece by piece so that only non-zero blocks of X1 enter
-  {
-    Op1Pieces whole;
-    whole.n = 1;
-    whole.v[0] = X1.v;
-    whole.c[0] = 1.0;
-    const Op1Pieces& pc = X1p ? *X1p : whole;
-    for (int k = 0; k < pc.n; ++k) {
-      const double c = pc.c[k];
-      contract(ws, c, pc.v[k], "xa", T2.v, "ayij", C2, "xyij");
-      contract(ws, -c, pc.v[k], "ya", T2.v, "axij", C2, "xyij");
-      contract(ws, -c, T2.v, "xyik", pc.v[k], "kj", C2, "xyij");
-      contract(ws, c, T2.v, "xyjk", pc.v[k], "ki", C2, "xyij");
+  auto exc_of = [&](const Tensor& C2) { return C2.v.iv[0].lo == P.lo && C2.v.iv[0].hi == P.hi; };
+  // on the excitation block the V part of the terms with three particle
+  // indices of V runs in density-fitted form
+  auto dfv_of = [&](const Tensor& C2) { return exc_of(C2) && df && X2.V && X2.cv != 0.0; };
+  for (int o = 0; o < nout; ++o) {
+    Tensor& C1 = *C1s[o];
+    Tensor& C2 = *C2s[o];
+    const bool dfv = dfv_of(C2);
+    // [X1, T1] one-body: X1 T1 - T1 X1
+    ws.tag = "c-x1";
+    contract(ws, 1.0, X1.v, "pr", T1.v, "rq", C1, "pq");
+    contract(ws, -1.0, T1.v, "pr", X1.v, "rq", C1, "pq");
+    // [X1, T2] one-body: (gamma X1 eta - eta X1 gamma)[i,a] T2[a,b,i,j]
+    {
+      Tensor M1 = mk(h, {G, G});
+      Tensor t1 = mk(h, {G, P});
+      contract(ws, 1.0, X1.v, "pq", e.v, "qa", t1, "pa");
+      contract(ws, 1.0, g.v, "ip", t1.v, "pa", M1, "ia");
+      Tensor t2 = mk(h, {G, H});
+      contract(ws, 1.0, X1.v, "pq", g.v, "qa", t2, "pa");
+      contract(ws, -1.0, e.v, "ip", t2.v, "pa", M1, "ia");
+      contract(ws, 1.0, M1.v, "ia", T2.v, "abij", C1, "bj");
     }
+    // [X1, T2] two-body, piece by piece so that only non-zero blocks of X1 enter
+    {
+      Op1Pieces whole;
+      whole.n = 1;
+      whole.v[0] = X1.v;
+      whole.c[0] = 1.0;
+      const Op1Pieces& pc = X1p ? *X1p : whole;
+      for (int k = 0; k < pc.n; ++k) {
+        const double c = pc.c[k];
+        contract(ws, c, pc.v[k], "xa", T2.v, "ayij", C2, "xyij");
+        contract(ws, -c, pc.v[k], "ya", T2.v, "axij", C2, "xyij");
+        contract(ws, -c, T2.v, "xyik", pc.v[k], "kj", C2, "xyij");
+        contract(ws, c, T2.v, "xyjk", pc.v[k], "ki", C2, "xyij");
+      }
+    }
+    // [X2, T1] one-body: X2[p,q,s,r] (gamma T1^T eta)[q,r]
+    ws.tag = "c-x2t1";
+    {
+      Tensor tmp = mk(h, {H, P});
+      contract(ws, 1.0, g.v, "qi", T1.v, "ai", tmp, "qa");
+      Tensor Mq = mk(h, {H, P});
+      contract(ws, 1.0, tmp.v, "qa", e.v, "ra", Mq, "qr");
+      contract_x2(ws, 1.0, X2, "pqsr", Mq.v, "qr", C1, "ps");
+    }
+    // [X2, T1] two-body
+    if (dfv) df_x2t1(h, T1, C2, X2.cv);
+    contract_x2(ws, 1.0, X2, "pqas", T1.v, "ar", C2, "pqrs", dfv);
+    contract_x2(ws, -1.0, X2, "pqar", T1.v, "as", C2, "pqrs", dfv);
+    contract_x2(ws, 1.0, X2, "qirs", T1.v, "pi", C2, "pqrs");
+    contract_x2(ws, -1.0, X2, "pirs", T1.v, "qi", C2, "pqrs");
   }
-  // [X2, T1] one-body: X2[p,q,s,r] (gamma T1^T eta)[q,r]
-  ws.tag = "c-x2t1";
-  {
-    Tensor tmp = mk(h, {H, P});
-    contract(ws, 1.0, g.v, "qi", T1.v, "ai", tmp, "qa");
-    Tensor Mq = mk(h, {H, P});
-    contract(ws, 1.0, tmp.v, "qa", e.v, "ra", Mq, "qr");
-    contract_x2(ws, 1.0, X2, "pqsr", Mq.v, "qr", C1, "ps");
-  }
-  // [X2, T1] two-body; on the excitation block the V part of the first two
-  // terms (three particle indices of V) in density-fitted form
-  const bool dfv = exc && df && X2.V && X2.cv != 0.0;
-  if (dfv) df_x2t1(h, T1, C2, X2.cv);
-  contract_x2(ws, 1.0, X2, "pqas", T1.v, "ar", C2, "pqrs", dfv);
-  contract_x2(ws, -1.0, X2, "pqar", T1.v, "as", C2, "pqrs", dfv);
-  contract_x2(ws, 1.0, X2, "qirs", T1.v, "pi", C2, "pqrs");
-  contract_x2(ws, -1.0, X2, "pirs", T1.v, "qi", C2, "pqrs");
   // [X2, T2] one-body with three single contractions
   ws.tag = "c-x2t2-1body";
   // dressed copies of T2, one chain at a time (each dressed in place after
@@ -603,12 +613,15 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
   // the memory peak of the large instances
   {
     Tensor D1 = dress(h, dress(h, dress(h, T2, 0, e), 1, e), 2, g);
-    if (dfv) df_vd_onebody(h, D1, C1, -0.5 * X2.cv);
-    contract_x2(ws, -0.5, X2, "pqrs", D1.v, "rsqj", C1, "pj", dfv);
+    for (int o = 0; o < nout; ++o) {
+      const bool dfv = dfv_of(*C2s[o]);
+      if (dfv) df_vd_onebody(h, D1, *C1s[o], -0.5 * X2.cv);
+      contract_x2(ws, -0.5, X2, "pqrs", D1.v, "rsqj", *C1s[o], "pj", dfv);
+    }
   }
   {
     Tensor D2 = dress(h, dress(h, dress(h, T2, 0, g), 1, g), 2, e);
-    contract_x2(ws, -0.5, X2, "pqrs", D2.v, "rsqj", C1, "pj");
+    for (int o = 0; o < nout; ++o) contract_x2(ws, -0.5, X2, "pqrs", D2.v, "rsqj", *C1s[o], "pj");
   }
   {
     // hole ladder 1/2 X2 (gamma gamma T2 - eta eta T2) as one product: the
@@ -619,135 +632,159 @@ void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, co
     Tensor D4 = dress(h, Nhh, 0, g);
     Tensor Ehh = dress(h, dress(h, T2, 2, g), 3, g);
     axpy(ws, -1.0, Nhh.v, "abij", Ehh, "abij");
-    contract_x2(ws, 0.5, X2, "pqrs", Ehh.v, "abpq", C2, "abrs");
+    for (int o = 0; o < nout; ++o) contract_x2(ws, 0.5, X2, "pqrs", Ehh.v, "abpq", *C2s[o], "abrs");
     axpy(ws, 1.0, Nhh.v, "abij", Ehh, "abij");
     Nhh.release();
     Tensor D3 = dress(h, std::move(Ehh), 0, e);
     axpy(ws, 1.0, D4.v, "abij", D3, "abij");
     D4.release();
-    contract_x2(ws, -0.5, X2, "pqrs", D3.v, "rbpq", C1, "bs");
+    for (int o = 0; o < nout; ++o) contract_x2(ws, -0.5, X2, "pqrs", D3.v, "rbpq", *C1s[o], "bs");
   }
-  // [X2, T2] one-body with a two-body cumulant
-  ws.tag = "c-cumulant";
-  if (h.na > 0) {
-    {
-      Tensor Y = mk(h, {P, A});
-      contract(ws, 1.0, T2.v, "abij", L2.v, "qbij", Y, "aq");
-      Tensor Z = dress(h, Y, 0, e);
-      contract_x2(ws, -0.5, X2, "pqrs", Z.v, "rq", C1, "ps");
-    }
-    {
-      Tensor Y = mk(h, {H, A});
-      contract(ws, 1.0, T2.v, "abij", L2.v, "abjr", Y, "ir");
-      Tensor Z = dress(h, Y, 0, g);
-      contract_x2(ws, -0.5, X2, "pqrs", Z.v, "qr", C1, "ps");
-    }
-    {
-      Tensor Y = mk_dense(h, {P, H, A, A});  // conserves a + s = i + q
-      contract(ws, 1.0, T2.v, "abij", L2.v, "qbjs", Y, "aiqs");
-      contract_x2(ws, -1.0, X2, "pqas", Y.v, "aiqs", C1, "pi");
-    }
-    {
-      Tensor Y = mk(h, {P, P, A, A});
-      contract(ws, 1.0, T2.v, "abij", L2.v, "pqij", Y, "abpq");
-      contract_x2(ws, -0.25, X2, "pqas", Y.v, "abpq", C1, "bs");
-    }
-    {
-      Tensor Y = mk(h, {P, A});
-      contract_x2(ws, 1.0, X2, "pqas", L2.v, "pqjs", Y, "aj");
-      contract(ws, -0.5, Y.v, "aj", T2.v, "abij", C1, "bi");
-    }
-    {
-      Tensor Y = mk(h, {C1.v.iv[0], H, A, A});
-      contract_x2(ws, 1.0, X2, "pirs", L2.v, "abrs", Y, "piab");
-      contract(ws, -0.25, Y.v, "piab", T2.v, "abij", C1, "pj");
-    }
-    {
-      Tensor Y = mk_dense(h, {P, H, A, A});  // conserves b + r = i + p
-      contract(ws, 1.0, T2.v, "abij", L2.v, "pajr", Y, "bipr");
-      contract_x2(ws, -1.0, X2, "pirs", Y.v, "bipr", C1, "bs");
-    }
-    {
-      Tensor Y = mk(h, {H, A});
-      contract_x2(ws, 1.0, X2, "pirs", L2.v, "pars", Y, "ia");
-      contract(ws, -0.5, Y.v, "ia", T2.v, "abij", C1, "bj");
+  for (int o = 0; o < nout; ++o) {
+    Tensor& C1 = *C1s[o];
+    // [X2, T2] one-body with a two-body cumulant
+    ws.tag = "c-cumulant";
+    if (h.na > 0) {
+      {
+        Tensor Y = mk(h, {P, A});
+        contract(ws, 1.0, T2.v, "abij", L2.v, "qbij", Y, "aq");
+        Tensor Z = dress(h, Y, 0, e);
+        contract_x2(ws, -0.5, X2, "pqrs", Z.v, "rq", C1, "ps");
+      }
+      {
+        Tensor Y = mk(h, {H, A});
+        contract(ws, 1.0, T2.v, "abij", L2.v, "abjr", Y, "ir");
+        Tensor Z = dress(h, Y, 0, g);
+        contract_x2(ws, -0.5, X2, "pqrs", Z.v, "qr", C1, "ps");
+      }
+      {
+        Tensor Y = mk_dense(h, {P, H, A, A});  // conserves a + s = i + q
+        contract(ws, 1.0, T2.v, "abij", L2.v, "qbjs", Y, "aiqs");
+        contract_x2(ws, -1.0, X2, "pqas", Y.v, "aiqs", C1, "pi");
+      }
+      {
+        Tensor Y = mk(h, {P, P, A, A});
+        contract(ws, 1.0, T2.v, "abij", L2.v, "pqij", Y, "abpq");
+        contract_x2(ws, -0.25, X2, "pqas", Y.v, "abpq", C1, "bs");
+      }
+      {
+        Tensor Y = mk(h, {P, A});
+        contract_x2(ws, 1.0, X2, "pqas", L2.v, "pqjs", Y, "aj");
+        contract(ws, -0.5, Y.v, "aj", T2.v, "abij", C1, "bi");
+      }
+      {
+        Tensor Y = mk(h, {C1.v.iv[0], H, A, A});
+        contract_x2(ws, 1.0, X2, "pirs", L2.v, "abrs", Y, "piab");
+        contract(ws, -0.25, Y.v, "piab", T2.v, "abij", C1, "pj");
+      }
+      {
+        Tensor Y = mk_dense(h, {P, H, A, A});  // conserves b + r = i + p
+        contract(ws, 1.0, T2.v, "abij", L2.v, "pajr", Y, "bipr");
+        contract_x2(ws, -1.0, X2, "pirs", Y.v, "bipr", C1, "bs");
+      }
+      {
+        Tensor Y = mk(h, {H, A});
+        contract_x2(ws, 1.0, X2, "pirs", L2.v, "pars", Y, "ia");
+        contract(ws, -0.5, Y.v, "ia", T2.v, "abij", C1, "bj");
+      }
     }
   }
   // [X2, T2] two-body: particle ladder 1/2 X2 T2 - X2[p,q,r,b] (gamma T2)[r,b,i,j]
   ws.tag = "c-x2t2-2body";
-  if (exc) {
-    // the V part of the all-particle block is never stored: DF ladder
-    if (X2.V && X2.cv != 0.0) {
-      if (!df) throw std::runtime_error("particle ladder of V needs the DF path");
-      df_ladder(h, T2, C2, X2.cv);
+  for (int o = 0; o < nout; ++o) {
+    Tensor& C2 = *C2s[o];
+    if (exc_of(C2)) {
+      // the V part of the all-particle block is never stored: DF ladder
+      if (X2.V && X2.cv != 0.0) {
+        if (!df) throw std::runtime_error("particle ladder of V needs the DF path");
+        df_ladder(h, T2, C2, X2.cv);
+      }
+    } else {
+      contract_x2(ws, 0.5, X2, "pqrs", T2.v, "rsij", C2, "pqij");
     }
-    Tensor gT2 = dress(h, T2, 0, g);
-    if (X2.W && X2.cw != 0.0) {
-      // W's excitation block [P,P,H,H] meets both terms only on its [A,A]
-      // second pair: one product with (1/2 T2 - gamma T2) on [A,A,H,H];
-      // its Hermitian image takes each term on its own
-      Iv box[4] = {A, A, H, H};
-      Tensor Y = make_tensor(ws, 4, box, true);
-      axpy(ws, 0.5, T2.v.sub(box), "rsij", Y, "rsij");
-      axpy(ws, -1.0, gT2.v.sub(box), "rsij", Y, "rsij");
-      contract(ws, X2.cw, w_place(*X2.W, 0), "pqrs", Y.v, "rsij", C2, "pqij");
-      contract(ws, 0.5 * X2.cw, w_place(*X2.W, 1), "pqrs", T2.v, "rsij", C2, "pqij");
-      contract(ws, -X2.cw, w_place(*X2.W, 1), "pqrb", gT2.v, "rbij", C2, "pqij");
-    }
-    if (X2.V && X2.cv != 0.0)
-      contract_x2(ws, -1.0, Op2{X2.V, X2.cv, nullptr, 0.0}, "pqrb", gT2.v, "rbij", C2, "pqij");
-  } else {
-    contract_x2(ws, 0.5, X2, "pqrs", T2.v, "rsij", C2, "pqij");
-    Tensor gT2 = dress(h, T2, 0, g);
-    contract_x2(ws, -1.0, X2, "pqrb", gT2.v, "rbij", C2, "pqij");
   }
-  // ring: K[x,y,u,w] = sum_{i,a} (Xbar - Xtilde)[x,i,a,w] T2[a,y,i,u], antisymmetrised.
-  // X2 is taken piece by piece (V, then W and its Hermitian image on their
-  // own boxes) so that no work is spent where a piece vanishes.
   {
-    ProfTag ring_tag(ws, "ring");
-    Iv xi = isect(exc ? P : H, C2.v.iv[0]), wi = isect(exc ? H : P, C2.v.iv[3]);
-    Iv want[4] = {xi, H, P, wi};
-    // y and u must land in C2's slots as well as in T2's
-    Iv kiv[4] = {xi, isect(P, C2.v.iv[1]), isect(H, C2.v.iv[2]), wi};
-    Tensor K = make_tensor(ws, 4, kiv, true);
-    // (Xbar - Xtilde) as one operand: Xtilde (eta on the hole slot, gamma on
-    // the particle slot) lives on the active box inside Xbar's
-    auto ring_piece = [&](const Tensor& Xs) {
-      Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
-      {
-        Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
-        axpy(ws, -1.0, Xt.v, "xiaw", Xb, "xiaw");
-      }
-      contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
-    };
-    if (X2.V && X2.cv != 0.0) {
-      // V covers the whole box: W's pieces are added into it, one product
-      Tensor Xs = make_tensor(ws, 4, want, true);
-      fetch_x2(ws, 1.0, Op2{X2.V, X2.cv, nullptr, 0.0}, Xs);
-      if (X2.W && X2.cw != 0.0)
-        for (int herm = 0; herm < 2; ++herm) axpy(ws, X2.cw, w_place(*X2.W, herm), "abcd", Xs, "abcd");
-      ring_piece(Xs);
-    } else if (X2.W && X2.cw != 0.0) {
-      for (int herm = 0; herm < 2; ++herm) {
-        View wp = w_place(*X2.W, herm);
-        Iv box[4];
-        bool empty = false;
-        for (int k = 0; k < 4; ++k) {
-          box[k] = isect(want[k], wp.iv[k]);
-          empty |= box[k].empty();
+    Tensor gT2 = dress(h, T2, 0, g);
+    for (int o = 0; o < nout; ++o) {
+      Tensor& C2 = *C2s[o];
+      if (exc_of(C2)) {
+        if (X2.W && X2.cw != 0.0) {
+          // W's excitation block [P,P,H,H] meets both terms only on its [A,A]
+          // second pair: one product with (1/2 T2 - gamma T2) on [A,A,H,H];
+          // its Hermitian image takes each term on its own
+          Iv box[4] = {A, A, H, H};
+          Tensor Y = make_tensor(ws, 4, box, true);
+          axpy(ws, 0.5, T2.v.sub(box), "rsij", Y, "rsij");
+          axpy(ws, -1.0, gT2.v.sub(box), "rsij", Y, "rsij");
+          contract(ws, X2.cw, w_place(*X2.W, 0), "pqrs", Y.v, "rsij", C2, "pqij");
+          contract(ws, 0.5 * X2.cw, w_place(*X2.W, 1), "pqrs", T2.v, "rsij", C2, "pqij");
+          contract(ws, -X2.cw, w_place(*X2.W, 1), "pqrb", gT2.v, "rbij", C2, "pqij");
         }
-        if (empty) continue;
-        Tensor Xs = make_tensor(ws, 4, box, true);
-        axpy(ws, X2.cw, wp, "abcd", Xs, "abcd");
-        ring_piece(Xs);
+        if (X2.V && X2.cv != 0.0)
+          contract_x2(ws, -1.0, Op2{X2.V, X2.cv, nullptr, 0.0}, "pqrb", gT2.v, "rbij", C2, "pqij");
+      } else {
+        contract_x2(ws, -1.0, X2, "pqrb", gT2.v, "rbij", C2, "pqij");
       }
     }
-    axpy(ws, 1.0, K.v, "xyuw", C2, "xyuw");
-    axpy(ws, -1.0, K.v, "xyuw", C2, "yxuw");
-    axpy(ws, -1.0, K.v, "xyuw", C2, "xywu");
-    axpy(ws, 1.0, K.v, "xyuw", C2, "yxwu");
   }
+  for (int o = 0; o < nout; ++o) {
+    Tensor& C2 = *C2s[o];
+    const bool exc = exc_of(C2);
+    // ring: K[x,y,u,w] = sum_{i,a} (Xbar - Xtilde)[x,i,a,w] T2[a,y,i,u], antisymmetrised.
+    // X2 is taken piece by piece (V, then W and its Hermitian image on their
+    // own boxes) so that no work is spent where a piece vanishes.
+    {
+      ProfTag ring_tag(ws, "ring");
+      Iv xi = isect(exc ? P : H, C2.v.iv[0]), wi = isect(exc ? H : P, C2.v.iv[3]);
+      Iv want[4] = {xi, H, P, wi};
+      // y and u must land in C2's slots as well as in T2's
+      Iv kiv[4] = {xi, isect(P, C2.v.iv[1]), isect(H, C2.v.iv[2]), wi};
+      Tensor K = make_tensor(ws, 4, kiv, true);
+      // (Xbar - Xtilde) as one operand: Xtilde (eta on the hole slot, gamma on
+      // the particle slot) lives on the active box inside Xbar's
+      auto ring_piece = [&](const Tensor& Xs) {
+        Tensor Xb = dress(h, dress(h, Xs, 1, g), 2, e);
+        {
+          Tensor Xt = dress(h, dress(h, Xs, 1, e), 2, g);
+          axpy(ws, -1.0, Xt.v, "xiaw", Xb, "xiaw");
+        }
+        contract(ws, 1.0, Xb.v, "xiaw", T2.v, "ayiu", K, "xyuw");
+      };
+      if (X2.V && X2.cv != 0.0) {
+        // V covers the whole box: W's pieces are added into it, one product
+        Tensor Xs = make_tensor(ws, 4, want, true);
+        fetch_x2(ws, 1.0, Op2{X2.V, X2.cv, nullptr, 0.0}, Xs);
+        if (X2.W && X2.cw != 0.0)
+          for (int herm = 0; herm < 2; ++herm) axpy(ws, X2.cw, w_place(*X2.W, herm), "abcd", Xs, "abcd");
+        ring_piece(Xs);
+      } else if (X2.W && X2.cw != 0.0) {
+        for (int herm = 0; herm < 2; ++herm) {
+          View wp = w_place(*X2.W, herm);
+          Iv box[4];
+          bool empty = false;
+          for (int k = 0; k < 4; ++k) {
+            box[k] = isect(want[k], wp.iv[k]);
+            empty |= box[k].empty();
+          }
+          if (empty) continue;
+          Tensor Xs = make_tensor(ws, 4, box, true);
+          axpy(ws, X2.cw, wp, "abcd", Xs, "abcd");
+          ring_piece(Xs);
+        }
+      }
+      axpy(ws, 1.0, K.v, "xyuw", C2, "xyuw");
+      axpy(ws, -1.0, K.v, "xyuw", C2, "yxuw");
+      axpy(ws, -1.0, K.v, "xyuw", C2, "xywu");
+      axpy(ws, 1.0, K.v, "xyuw", C2, "yxwu");
+    }
+  }
+}
+
+void commutator(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, const Tensor& T2, Tensor& C1,
+                Tensor& C2, bool df, const Op1Pieces* X1p) {
+  Tensor* c1[1] = {&C1};
+  Tensor* c2[1] = {&C2};
+  commutator(h, X1, X2, T1, T2, c1, c2, 1, df, X1p);
 }
 
 // excitation blocks of [X, T - T^+] = [X, T] + [X, T]^+ (X Hermitian)
@@ -757,11 +794,13 @@ void commutator_A(Handle& h, const Tensor& X1, const Op2& X2, const Tensor& T1, 
   O2 = mk(h, {h.P, h.P, h.H, h.H});
   // excitation blocks straight into O1, O2; the de-excitation blocks [H H P P]
   // land in O2 through a slot-permuted alias (the commutator only accumulates)
-  commutator(h, X1, X2, T1, T2, O1, O2, df, X1p);
+  // (both in one pass, so that the dressed copies of T2 are formed once)
   const int perm[4] = {2, 3, 0, 1};
   Tensor C1d = mk(h, {h.H, h.P});
   Tensor C2d = alias_permuted(O2, perm);
-  commutator(h, X1, X2, T1, T2, C1d, C2d, df, X1p);
+  Tensor* c1[2] = {&O1, &C1d};
+  Tensor* c2[2] = {&O2, &C2d};
+  commutator(h, X1, X2, T1, T2, c1, c2, 2, df, X1p);
   merge_alias_mask(O2, C2d, perm);
   axpy(h.ws, 1.0, C1d.v, "ia", O1, "ai");
 }
