@@ -280,11 +280,11 @@ int dsrg_df_ladder(int n, int naux, int p0, int np, int nh, const double *B, con
  * np^3 <= 2^22 (np <= 161) is required; larger np returns DSRG_ERR_ARG with
  * a message.  Set-up: the first call on a device (and the first call after
  * that device's context changed, e.g. after cudaDeviceReset) looks up the
- * array's device address with the device current; make that first call
- * before any stream capture.  All calls share the array and it keeps the
- * last call's contents (each batch clears what it accumulates into); calls
- * that overlap on the GPU (other streams, other host threads) race on it and
- * must be serialised by the caller.  Synchronises `stream`.
+ * array's device address with the device current.  All calls share the
+ * array and it keeps the last call's contents (each batch clears what it
+ * accumulates into); calls that overlap on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller.
+ * Synchronises `stream`.
  */
 int dsrg_df_ladder_noalloc(int n, int naux, int p0, int np, int nh, const double *B, const double *t, double *L,
                            void *stream);
