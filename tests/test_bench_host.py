@@ -68,3 +68,26 @@ def test_scan_groups_cover_every_point_within_budget():
             assert len(g) == 1 or sum(sizes[k] for k in g) <= budget
     assert len(bench.scan_groups(insts, 3e11)) == 1
     assert all(len(g) == 1 for g in bench.scan_groups(insts, 1.0))
+
+
+def test_profiled_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while the
+    split kernel's source is the one the counters were taken on."""
+    import shutil
+    wl = "cas88_c30_v300_q1200"
+    traffic, src = bench.profiled_traffic(wl)
+    assert traffic is not None and traffic > 0, src
+    assert src == f"profiles/k_ozaki_mma_{wl}.md"
+    # a copy of the tree whose kernel source differs by one byte
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_1701_02011_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", f"k_ozaki_mma_{wl}.md"), tmp_path / "profiles")
+    kernel = open(os.path.join(bench.ROOT, "paper_1701_02011_gb300", "csrc", "ozaki.cu"), "rb").read()
+    (csrc / "ozaki.cu").write_bytes(kernel)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic(wl)[0] == traffic
+    (csrc / "ozaki.cu").write_bytes(kernel + b"\n")
+    t2, why = bench.profiled_traffic(wl)
+    assert t2 is None and "predates" in why
+    assert bench.profiled_traffic("no_such_workload") == (None, None)
